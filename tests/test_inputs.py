@@ -1,0 +1,72 @@
+"""Seeded workload generators: geometry checks against closed forms."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from paper_2506_15411_gb300 import inputs
+
+LAM = 1.064e-6
+
+
+def test_sphere_volume_fraction_integrates_to_sphere_volume():
+    n, pitch, a = 40, LAM / 8, 1.3e-6
+    eps = inputs.sphere_eps(n, n, n, pitch, a, 1.5, 1.0)
+    frac = (eps.astype(np.float64) - 1.0) / (1.5 ** 2 - 1.0)
+    vol = frac.sum() * pitch ** 3
+    assert abs(vol - 4 / 3 * math.pi * a ** 3) < 2e-3 * 4 / 3 * math.pi * a ** 3
+    assert eps.dtype == np.float32 and eps.min() >= 1.0 and eps.max() <= 2.25 + 1e-6
+    # symmetric under reflection about the centre
+    assert np.allclose(eps, eps[::-1, ::-1, ::-1])
+
+
+def test_focal_length_from_numerical_aperture():
+    f = inputs.focal_length(16e-6, 0.84)
+    assert math.isclose(math.sin(math.atan(8e-6 / f)), 0.84, rel_tol=1e-12)
+    assert abs(f - 5.17e-6) < 0.01e-6
+
+
+def test_fresnel_kinoform_phase():
+    """Thickness wraps the focusing phase: (n-1) k h + k (sqrt(r^2+f^2) - f) = 0 mod 2 pi."""
+    D, NA, n = 16e-6, 0.84, 1.5
+    r = np.linspace(0, D / 2, 2001)
+    h = inputs.fresnel_height(r, LAM, D, NA, n)
+    f = inputs.focal_length(D, NA)
+    k = 2 * math.pi / LAM
+    phase = (n - 1) * k * h + k * (np.sqrt(r ** 2 + f ** 2) - f)
+    wrapped = np.mod(phase + 1e-9, 2 * math.pi)
+    assert np.all((wrapped < 1e-6) | (wrapped > 2 * math.pi - 1e-6))
+    assert h.max() <= LAM / (n - 1) + 1e-15 and h.min() >= 0
+    assert inputs.fresnel_height(np.array([D / 2 * 1.01]), LAM, D, NA, n)[0] == 0.0
+
+
+def test_height_to_eps_subpixel_fractions():
+    h = np.array([[0.0, 0.5, 1.0, 2.25]]) * 1e-7
+    eps = inputs.height_to_eps(h, 6, 1e-7, 2, 1.5, 1.0)
+    frac = (eps - 1.0) / 1.25
+    assert np.allclose(frac[:2], 0)
+    assert np.allclose(frac[2:, 0, 0], [0, 0, 0, 0])
+    assert np.allclose(frac[2:, 0, 1], [0.5, 0, 0, 0])
+    assert np.allclose(frac[2:, 0, 2], [1, 0, 0, 0])
+    assert np.allclose(frac[2:, 0, 3], [1, 1, 0.25, 0])
+    assert np.allclose(frac.sum(axis=0)[0] * 1e-7, h[0])
+
+
+def test_lens_workload_layout():
+    wl = inputs.fresnel_lens_workload(275, 275, 315, LAM / 16, LAM, 16e-6, 0.84, 1.5)
+    assert wl.pad_lo == (16, 16, 96) and wl.eps.shape == (315, 275, 275)
+    assert wl.z_base == wl.z_source + 2 and wl.r0[:2] == (137, 137)
+    assert wl.r0[2] == wl.z_base + round(inputs.focal_length(16e-6, 0.84) / (LAM / 16))
+    # interior spans the lens diameter (243 voxels of 66.5 nm ~ 16.2 um)
+    assert (275 - 32) * LAM / 16 > 16e-6
+
+
+def test_seeded_generators_are_reproducible():
+    a = inputs.random_field(5, 4, 3, seed=9)
+    b = inputs.random_field(5, 4, 3, seed=9)
+    assert np.array_equal(a, b) and a.shape == (3, 3, 4, 5)
+    e1, reg = inputs.design_slab_eps(64, 64, 48, LAM / 8, LAM, slab=(32, 32, 8), z_base=10)
+    e2, _ = inputs.design_slab_eps(64, 64, 48, LAM / 8, LAM, slab=(32, 32, 8), z_base=10)
+    assert np.array_equal(e1, e2)
+    assert e1[reg].min() >= 1.0 and e1[reg].max() <= 2.25 + 1e-6
