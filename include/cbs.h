@@ -1,0 +1,160 @@
+/*
+ * cbs.h -- C ABI of the GB300 vector convergent Born series (CBS) solver.
+ *
+ * The solver computes the total electric field E of the monochromatic Maxwell problem
+ *
+ *     curl curl E - k(r)^2 E = S,        k(r)^2 = k_vac^2 (eps_r(r) + i sigma(r)),
+ *
+ * on a periodic voxel grid surrounded by absorbing layers, and the adjoint-field gradient
+ * of the focal intensity |E(r0)|^2 with respect to eps_r.  This is the forward/adjoint
+ * machinery of arXiv 2506.15411 (the CBS of its refs. [25], [26], run inside absorbing
+ * layers [lambda, lambda, 6 lambda], Fig. 1 benchmark paragraph; figure of merit and its
+ * gradient, Fig. 2 caption and the figure-of-merit paragraph).  The series is
+ *
+ *     gamma = (i / epsilon) V,   V = k^2 - k0^2 - i epsilon,
+ *     E <- E - gamma [E - G (V E + S)],
+ *
+ * with G the dyadic Green operator of curl curl - (k0^2 + i epsilon), applied in k-space by
+ * 3D FFTs of the three field components.
+ *
+ * Conventions shared by every call
+ *   - Time factor exp(-i w t); outgoing waves go as exp(+i k r).
+ *   - Grid arrays are C-order [nz][ny][nx] (x fastest).  Fields are complex64 (interleaved
+ *     float re, im) of shape [3][nz][ny][nx], component order (x, y, z): 24 bytes a voxel.
+ *   - Every pointer named *_dev is device memory of the plan's device, owned by the
+ *     caller, contiguous, and at least 8-byte aligned; the plan never frees it.
+ *   - Work is enqueued on desc.cuda_stream (blocks of iterations are captured there as CUDA
+ *     graphs, so no other thread may use that stream during a call); with a NULL stream the
+ *     plan owns a stream that first waits for the legacy stream.  The solve calls return
+ *     when their result is complete on the device (the host needs the residual to decide
+ *     convergence).
+ *   - Return value: CBS_OK (0) or a negative CBS_ERR_* code; cbs_last_error() gives a
+ *     message (thread-local, valid until the next call on that thread).
+ *   - A plan is not thread-safe: calls on one plan must not overlap.
+ */
+#ifndef CBS_GB300_H
+#define CBS_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CBS_OK 0
+#define CBS_ERR_ARG (-1)            /* bad argument: dims, radix, pads, null pointer, ... */
+#define CBS_ERR_OOM (-2)            /* device allocation failed */
+#define CBS_ERR_NOT_CONVERGED (-3)  /* tol > 0 and max_iter reached; E holds the last iterate */
+#define CBS_ERR_DIVERGED (-4)       /* residual non-finite or grew 1e4-fold; E is garbage */
+#define CBS_ERR_CUDA (-5)           /* a CUDA runtime call failed */
+#define CBS_ERR_STATE (-6)          /* call out of order, e.g. no permittivity set yet */
+#define CBS_ERR_STAGNATED (-7)      /* tol > 0 not reached and the residual stopped falling
+                                       (no new 1 % minimum over max(1000, it/4) iterations):
+                                       the FP32 rounding floor; E holds the last iterate */
+
+typedef struct cbs_plan_s* cbs_plan_t;
+
+/* Problem and solver description (copied by cbs_plan). */
+typedef struct {
+  int nx, ny, nz;         /* grid, including the absorbing layers; each a product of
+                             2, 3, 5, 7, 11, 13 and at most 1024 */
+  double pitch_m;         /* voxel pitch [m] (isotropic) */
+  double lambda_m;        /* vacuum wavelength [m] */
+  double n_bg;            /* background index; sets the layer strength */
+  int pad_lo[3];          /* absorbing-layer thickness in voxels on the low faces (x,y,z) */
+  int pad_hi[3];          /* ... and on the high faces; each pad <= half the axis */
+  double tol;             /* stop when ||delta_k|| / ||delta_0|| <= tol; tol <= 0 runs
+                             exactly max_iter iterations */
+  int max_iter;           /* > 0 */
+  int check_every;        /* iterations between residual checks on the host (>= 1) */
+  void* cuda_stream;      /* cudaStream_t the plan works on; NULL = legacy (see above) */
+} cbs_plan_desc;
+
+#define CBS_SRC_PLANE_WAVE 0  /* current sheet on plane z_plane launching pol * exp(ik|z-z_s|) */
+#define CBS_SRC_POINT 1       /* raw value pol at voxel r0 (a dipole p is pol = p / pitch^3) */
+#define CBS_SRC_USER 2        /* caller's S, complex64 [3][nz][ny][nx] on the device */
+
+/* Source term S of the forward problem. */
+typedef struct {
+  int kind;                 /* CBS_SRC_* */
+  double pol[3][2];         /* complex polarisation (re, im) for x, y, z */
+  int z_plane;              /* plane-wave sheet; < 0 selects pad_lo[2] */
+  int r0[3];                /* point-source voxel (x, y, z) */
+  const void* user_src_dev; /* CBS_SRC_USER only */
+  int warm_start;           /* nonzero: E_dev holds the initial guess; else E starts at 0 */
+} cbs_source;
+
+/* Outcome of one solve (always filled when the pointer is not NULL). */
+typedef struct {
+  int iters;         /* iterations run */
+  double rel_resid;  /* ||delta_last|| / ||delta_0|| (FP64 sums on the device) */
+  double resid0;     /* ||delta_0|| */
+  double seconds;    /* host wall time of the call */
+  int status;        /* return code of the call */
+} cbs_stats;
+
+/* Create a plan: checks the description, factors each axis into FFT radices and allocates
+ * the plan's device memory (potential V: 8 B/voxel; k-space workspace W: 24 B/voxel;
+ * twiddles and reduction scratch).  *out receives the plan.  Errors: CBS_ERR_ARG,
+ * CBS_ERR_OOM, CBS_ERR_CUDA. */
+int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc);
+
+/* Set the relative permittivity (real, float32 [nz][ny][nx], layers included; the plan
+ * adds the absorption inside the pads).  Computes the splitting
+ * k0^2 = (min Re k^2 + max Re k^2)/2, epsilon = max |k^2 - k0^2| with FP64 reductions on the
+ * device and stores V.  Errors: CBS_ERR_ARG (NULL, non-finite or zero-epsilon input),
+ * CBS_ERR_CUDA. */
+int cbs_set_permittivity(cbs_plan_t plan, const float* eps_real_dev);
+
+/* The splitting chosen by the last cbs_set_permittivity, in SI units [1/m^2]. */
+int cbs_get_splitting(cbs_plan_t plan, double* k0sq, double* epsilon);
+
+/* Change the stopping rule of later solves (same meaning as in cbs_plan_desc). */
+int cbs_set_solver(cbs_plan_t plan, double tol, int max_iter, int check_every);
+
+/* Forward solve: iterate the series for source *src into E_dev (complex64 [3][nz][ny][nx]).
+ * Returns CBS_OK, CBS_ERR_NOT_CONVERGED (tol > 0 not reached in max_iter; E_dev holds the
+ * last iterate), CBS_ERR_STAGNATED (residual at its FP32 floor above tol), CBS_ERR_DIVERGED,
+ * CBS_ERR_ARG, CBS_ERR_STATE or CBS_ERR_CUDA. */
+int cbs_forward(cbs_plan_t plan, const cbs_source* src, void* E_dev, cbs_stats* stats);
+
+/* Adjoint solve for the figure of merit |E(r0)|^2: E_adj = A^{-1}[conj(E(r0)) delta_r0],
+ * the same series with a raw point source conj(E(r0)) read from E_dev on the device
+ * (A = curl curl - k^2 is complex symmetric).  r0 = (x, y, z) voxel.  Eadj_dev starts at 0.
+ * Return codes as cbs_forward. */
+int cbs_adjoint(cbs_plan_t plan, const int r0[3], const void* E_dev, void* Eadj_dev,
+                cbs_stats* stats);
+
+/* Gradient dL/d eps_r(r) = 2 k_vac^2 Re[E_adj(r) . E(r)] into grad_dev (float32
+ * [nz][ny][nx]); when r0 and objective are not NULL also *objective = |E(r0)|^2 (FP64).
+ * Errors: CBS_ERR_ARG, CBS_ERR_CUDA. */
+int cbs_gradient(cbs_plan_t plan, const void* E_dev, const void* Eadj_dev, const int r0[3],
+                 float* grad_dev, double* objective);
+
+/* One design iteration from HOST buffers: copies eps (float32 [nz][ny][nx]) to the device,
+ * sets it, runs the forward solve for *src into a plan-owned field, the adjoint solve for
+ * |E(r0)|^2 and the gradient, and copies the gradient back into grad_host (float32
+ * [nz][ny][nx]) and the objective into *objective.  The plan allocates its two field
+ * buffers (48 B/voxel) and staging on first use.  fwd/adj may be NULL.  Return codes as
+ * cbs_forward (the first failing step). */
+int cbs_design_step_host(cbs_plan_t plan, const float* eps_host, const cbs_source* src,
+                         const int r0[3], float* grad_host, double* objective,
+                         cbs_stats* fwd, cbs_stats* adj);
+
+/* Pass timing.  With profiling on, each block of iterations records CUDA events on the
+ * plan's stream around the five launches of its last iteration (also inside the replayed
+ * graphs); cbs_pass_times returns, per pass (0 x forward, 1 y forward, 2 z + k-space
+ * multiply, 3 y inverse, 4 x inverse + update), the summed event time in ms and the number
+ * of timed launches since the last reset.  Toggling drops the cached graphs.  Errors:
+ * CBS_ERR_ARG, CBS_ERR_CUDA. */
+int cbs_set_profiling(cbs_plan_t plan, int on);
+int cbs_pass_times(cbs_plan_t plan, double ms_total[5], long long launches[5], int reset);
+
+/* Free the plan and its device memory (NULL is a no-op). */
+void cbs_destroy(cbs_plan_t plan);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* cbs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CBS_GB300_H */

@@ -1,0 +1,100 @@
+"""ctypes binding of libcbs.so (the C ABI in include/cbs.h), with the same names.
+
+Argument marshalling only: every step of a solve runs in the CUDA library.  Importing this
+module loads the library and raises if it is missing; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, Structure, c_double, c_float, c_int, c_void_p
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libcbs.so")
+
+CBS_OK = 0
+CBS_ERR_ARG = -1
+CBS_ERR_OOM = -2
+CBS_ERR_NOT_CONVERGED = -3
+CBS_ERR_DIVERGED = -4
+CBS_ERR_CUDA = -5
+CBS_ERR_STATE = -6
+CBS_ERR_STAGNATED = -7
+
+CBS_SRC_PLANE_WAVE = 0
+CBS_SRC_POINT = 1
+CBS_SRC_USER = 2
+
+# Every symbol include/cbs.h declares.
+EXPORTS = ("cbs_plan", "cbs_set_permittivity", "cbs_get_splitting", "cbs_set_solver",
+           "cbs_forward", "cbs_adjoint", "cbs_gradient", "cbs_design_step_host",
+           "cbs_set_profiling", "cbs_pass_times", "cbs_destroy", "cbs_last_error")
+
+PASS_NAMES = ("k_xpass_fwd", "k_ypass_fwd", "k_zpass_green", "k_ypass_inv", "k_xpass_inv_update")
+
+
+class cbs_plan_desc(Structure):
+    _fields_ = [("nx", c_int), ("ny", c_int), ("nz", c_int),
+                ("pitch_m", c_double), ("lambda_m", c_double), ("n_bg", c_double),
+                ("pad_lo", c_int * 3), ("pad_hi", c_int * 3),
+                ("tol", c_double), ("max_iter", c_int), ("check_every", c_int),
+                ("cuda_stream", c_void_p)]
+
+
+class cbs_source(Structure):
+    _fields_ = [("kind", c_int), ("pol", (c_double * 2) * 3), ("z_plane", c_int),
+                ("r0", c_int * 3), ("user_src_dev", c_void_p), ("warm_start", c_int)]
+
+
+class cbs_stats(Structure):
+    _fields_ = [("iters", c_int), ("rel_resid", c_double), ("resid0", c_double),
+                ("seconds", c_double), ("status", c_int)]
+
+
+class CBSError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"CBS error {code}: {msg}")
+        self.code = code
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_2506_15411_gb300.build`")
+    lib = ctypes.CDLL(path)
+    P = c_void_p
+    sig = {
+        "cbs_plan": (c_int, [POINTER(c_void_p), POINTER(cbs_plan_desc)]),
+        "cbs_set_permittivity": (c_int, [P, P]),
+        "cbs_get_splitting": (c_int, [P, POINTER(c_double), POINTER(c_double)]),
+        "cbs_set_solver": (c_int, [P, c_double, c_int, c_int]),
+        "cbs_forward": (c_int, [P, POINTER(cbs_source), P, POINTER(cbs_stats)]),
+        "cbs_adjoint": (c_int, [P, POINTER(c_int * 3), P, P, POINTER(cbs_stats)]),
+        "cbs_gradient": (c_int, [P, P, P, POINTER(c_int * 3), P, POINTER(c_double)]),
+        "cbs_design_step_host": (c_int, [P, P, POINTER(cbs_source), POINTER(c_int * 3), P,
+                                         POINTER(c_double), POINTER(cbs_stats), POINTER(cbs_stats)]),
+        "cbs_set_profiling": (c_int, [P, c_int]),
+        "cbs_pass_times": (c_int, [P, POINTER(c_double * 5), POINTER(ctypes.c_longlong * 5), c_int]),
+        "cbs_destroy": (None, [P]),
+        "cbs_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load()
+    return _lib
+
+
+def check(rc: int, allow=(CBS_OK,)) -> int:
+    if rc not in allow:
+        raise CBSError(rc, lib().cbs_last_error().decode())
+    return rc

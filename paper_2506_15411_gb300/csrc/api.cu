@@ -1,0 +1,750 @@
+// api.cu -- host side of the C ABI declared in include/cbs.h: plans, the iteration loop with
+// its residual checks, the adjoint and gradient calls.
+//
+// One CBS iteration (refs. [25], [26] of arXiv 2506.15411) is five kernel launches on the
+// plan's stream:
+//   1. x pass     W = FFT_x(V E + S)
+//   2. y pass     W = FFT_y(W)
+//   3. z pass     W = IFFT_z(G(p) FFT_z(W)) / N
+//   4. y pass     W = IFFT_y(W)
+//   5. x pass     W = IFFT_x(W); delta = gamma (E - W); E -= delta; sum |delta|^2 (FP64)
+// Every `check_every` iterations the host reads the FP64 residual sums and decides whether
+// to stop; a full block of iterations is replayed from a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <string>
+#include <vector>
+
+#include "../../include/cbs.h"
+#include "cbs_internal.h"
+
+namespace cbs {
+cudaError_t xpass_set_smem_limit(int bytes);
+cudaError_t yzpass_set_smem_limit(int bytes);
+}  // namespace cbs
+
+using namespace cbs;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(CBS_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));         \
+  } while (0)
+
+constexpr double kPiD = 3.14159265358979323846;
+constexpr int kMaxN = 1024;
+
+// Factor n into the supported radices (at most max_radix): fewest stages first, then the
+// largest smallest radix (fewest threads per transform).  Radices are stored largest first.
+bool factor_axis(int n, int max_radix, AxisPlan& out) {
+  static const int cand[] = {16, 13, 12, 11, 10, 9, 8, 7, 6, 5, 4, 3, 2};
+  out = AxisPlan{};
+  out.n = n;
+  if (n == 1) {
+    out.ns = 1;
+    out.r[0] = 1;
+    out.T = 1;
+    return true;
+  }
+  std::vector<int> cur, best;
+  std::function<void(int, int)> dfs;
+  auto better = [&](const std::vector<int>& a, const std::vector<int>& b) {
+    if (b.empty()) return true;
+    if (a.size() != b.size()) return a.size() < b.size();
+    const int ma = *std::min_element(a.begin(), a.end());
+    const int mb = *std::min_element(b.begin(), b.end());
+    return ma > mb;
+  };
+  dfs = [&](int rem, int maxr) {
+    if (rem == 1) {
+      if (better(cur, best)) best = cur;
+      return;
+    }
+    if ((int)cur.size() >= kMaxStages) return;
+    for (int r : cand) {
+      if (r > maxr || r > max_radix || rem % r) continue;
+      cur.push_back(r);
+      dfs(rem / r, r);
+      cur.pop_back();
+    }
+  };
+  dfs(n, 1 << 30);
+  if (best.empty()) return false;
+  out.ns = (int)best.size();
+  int rmin = 1 << 30;
+  for (int i = 0; i < out.ns; ++i) {
+    out.r[i] = best[i];
+    rmin = std::min(rmin, best[i]);
+  }
+  out.T = n / rmin;
+  return true;
+}
+
+// Device table of an axis plan: per stage {r, Ns, n / r, n / (Ns r)}.
+std::vector<int4> stage_table(const AxisPlan& ap) {
+  std::vector<int4> t(kMaxStages, make_int4(1, 1, 1, 1));
+  int Ns = 1;
+  for (int q = 0; q < ap.ns; ++q) {
+    const int r = ap.r[q];
+    t[q] = make_int4(r, Ns, ap.n / r, ap.n / (Ns * r));
+    Ns *= r;
+  }
+  return t;
+}
+
+int pow2_ceil(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+// A captured block of iterations bakes in the field pointer and the whole source.
+struct GraphEntry {
+  float2* E;
+  SourceArgs src;
+  int iters;
+  cudaGraphExec_t exec;
+};
+
+bool same_source(const SourceArgs& a, const SourceArgs& b) {
+  if (a.kind != b.kind || a.zp != b.zp || a.px != b.px || a.py != b.py || a.pz != b.pz ||
+      a.amp_dev != b.amp_dev || a.user != b.user || a.user_scale != b.user_scale)
+    return false;
+  for (int c = 0; c < 3; ++c)
+    if (a.amp[c].x != b.amp[c].x || a.amp[c].y != b.amp[c].y) return false;
+  return true;
+}
+
+}  // namespace
+
+struct cbs_plan_s {
+  cbs_plan_desc d{};
+  int device = 0;
+  cudaStream_t user_stream = nullptr;
+  cudaStream_t stream = nullptr;   // the caller's stream, or an owned one for NULL (legacy)
+  bool own_stream = false;
+  cudaEvent_t ev = nullptr;
+  IterArgs base{};
+  size_t N = 0;
+  double pitch = 0, kvac = 0;
+  // device memory owned by the plan
+  float2* V = nullptr;
+  float2* W = nullptr;
+  float2* tw = nullptr;
+  int4* stages = nullptr;
+  double* partials = nullptr;
+  unsigned* counter = nullptr;
+  double* hist = nullptr;
+  float2* adj_amp = nullptr;
+  double* dobj = nullptr;
+  double *sx = nullptr, *sy = nullptr, *sz = nullptr;
+  // set-up scratch
+  float *pmin = nullptr, *pmax = nullptr;
+  int* pbad = nullptr;
+  double* pdev = nullptr;
+  int red_blocks = 0;
+  // host staging (pinned)
+  double* hist_host = nullptr;
+  // host-buffer design step
+  float* eps_dev = nullptr;
+  float2* Ef = nullptr;
+  float2* Ea = nullptr;
+  float* grad_dev = nullptr;
+  // splitting (scaled units)
+  bool have_eps = false;
+  double k0sq_s = 0, eps_s = 0;
+  // graphs of one block of check_every iterations, per (E, source) binding
+  std::vector<GraphEntry> graphs;
+  // pass timing (events around the launches of the last iteration of each block)
+  bool profiling = false;
+  cudaEvent_t pev[6] = {};
+  double pass_ms[5] = {};
+  long long pass_n[5] = {};
+};
+
+namespace {
+
+void drop_graphs(cbs_plan_s* p) {
+  for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
+  p->graphs.clear();
+}
+
+int sync_in(cbs_plan_s* p) {
+  CK(cudaSetDevice(p->device));
+  if (p->own_stream) {
+    CK(cudaEventRecord(p->ev, p->user_stream));
+    CK(cudaStreamWaitEvent(p->stream, p->ev, 0));
+  }
+  return CBS_OK;
+}
+
+// The five launches of one iteration; with ev != null, events ev[0..5] bracket them.
+int launch_iteration(const IterArgs& a, cudaStream_t s, cudaEvent_t* ev) {
+  if (ev) CK(cudaEventRecord(ev[0], s));
+  CK(launch_xpass_fwd(a, s));
+  if (ev) CK(cudaEventRecord(ev[1], s));
+  CK(launch_ypass(a, false, s));
+  if (ev) CK(cudaEventRecord(ev[2], s));
+  CK(launch_zpass_green(a, s));
+  if (ev) CK(cudaEventRecord(ev[3], s));
+  CK(launch_ypass(a, true, s));
+  if (ev) CK(cudaEventRecord(ev[4], s));
+  CK(launch_xpass_inv_update(a, s));
+  if (ev) CK(cudaEventRecord(ev[5], s));
+  return CBS_OK;
+}
+
+// Iterations k0 .. k1-1 of a block (residual slots k0 .. k1-1); with profiling on, the
+// block's last iteration (slot m-1) is bracketed by the timing events.
+int launch_range(cbs_plan_s* p, const IterArgs& a0, int k0, int k1, int m) {
+  IterArgs a = a0;
+  for (int k = k0; k < k1; ++k) {
+    a.slot = k;
+    int rc = launch_iteration(a, p->stream, (p->profiling && k == m - 1) ? p->pev : nullptr);
+    if (rc) return rc;
+  }
+  return CBS_OK;
+}
+
+// After a block has completed: add its timed iteration to the per-pass totals.
+int collect_pass_times(cbs_plan_s* p) {
+  if (!p->profiling) return CBS_OK;
+  for (int i = 0; i < 5; ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, p->pev[i], p->pev[i + 1]));
+    p->pass_ms[i] += ms;
+    p->pass_n[i] += 1;
+  }
+  return CBS_OK;
+}
+
+// Run iterations 0 .. n-1 of a block from a cached graph (captured on first use; event
+// records are kept out of graphs because events recorded by graph nodes cannot be timed).
+int graph_block(cbs_plan_s* p, const IterArgs& a, int n, bool& used) {
+  used = false;
+  cudaGraphExec_t exec = nullptr;
+  for (auto& g : p->graphs)
+    if (g.E == a.E && g.iters == n && same_source(g.src, a.src)) exec = g.exec;
+  if (!exec) {
+    if (p->graphs.size() >= 8) drop_graphs(p);
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = launch_range(p, a, 0, n, n + 1);
+    cudaGraph_t captured = nullptr;
+    cudaError_t e = cudaStreamEndCapture(p->stream, &captured);
+    if (rc) {
+      if (captured) cudaGraphDestroy(captured);
+      return rc;
+    }
+    if (e != cudaSuccess) return fail(CBS_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    g = captured;
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(CBS_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    p->graphs.push_back(GraphEntry{a.E, a.src, n, ex});
+    exec = ex;
+  }
+  CK(cudaGraphLaunch(exec, p->stream));
+  used = true;
+  return CBS_OK;
+}
+
+// Source in the kernels' scaled units (k^2 quantities times pitch^2).
+int make_source(cbs_plan_s* p, const cbs_source* src, SourceArgs& s) {
+  s = SourceArgs{};
+  s.kind = src->kind;
+  const double h = p->pitch;
+  if (src->kind == CBS_SRC_PLANE_WAVE) {
+    s.zp = src->z_plane < 0 ? p->d.pad_lo[2] : src->z_plane;
+    if (s.zp >= p->d.nz) return fail(CBS_ERR_ARG, "z_plane %d outside the grid", s.zp);
+    // S = pol * (-2 i k_b / pitch); scaled by pitch^2: pol * (-2 i k_b pitch)
+    const double kb = p->kvac * p->d.n_bg * h;
+    for (int c = 0; c < 3; ++c) {
+      const double re = src->pol[c][0], im = src->pol[c][1];
+      s.amp[c] = make_float2((float)(2.0 * kb * im), (float)(-2.0 * kb * re));
+    }
+  } else if (src->kind == CBS_SRC_POINT) {
+    const int* r = src->r0;
+    if (r[0] < 0 || r[0] >= p->d.nx || r[1] < 0 || r[1] >= p->d.ny || r[2] < 0 || r[2] >= p->d.nz)
+      return fail(CBS_ERR_ARG, "point source (%d,%d,%d) outside the grid", r[0], r[1], r[2]);
+    s.px = r[0];
+    s.py = r[1];
+    s.pz = r[2];
+    for (int c = 0; c < 3; ++c)
+      s.amp[c] = make_float2((float)(src->pol[c][0] * h * h), (float)(src->pol[c][1] * h * h));
+  } else if (src->kind == CBS_SRC_USER) {
+    if (!src->user_src_dev) return fail(CBS_ERR_ARG, "user source pointer is NULL");
+    s.user = static_cast<const float2*>(src->user_src_dev);
+    s.user_scale = (float)(h * h);
+  } else {
+    return fail(CBS_ERR_ARG, "unknown source kind %d", src->kind);
+  }
+  return CBS_OK;
+}
+
+int run_series(cbs_plan_s* p, float2* E, const SourceArgs& src, bool warm, cbs_stats* st) {
+  const auto t0 = std::chrono::steady_clock::now();
+  cbs_stats local{};
+  cbs_stats* S = st ? st : &local;
+  *S = cbs_stats{};
+  if (!p->have_eps) return S->status = fail(CBS_ERR_STATE, "cbs_set_permittivity has not been called");
+  IterArgs a = p->base;
+  a.E = E;
+  a.src = src;
+  int rc = CBS_OK;
+  if (!warm) {
+    cudaError_t e = cudaMemsetAsync(E, 0, 3 * p->N * sizeof(float2), p->stream);
+    if (e != cudaSuccess) return S->status = fail(CBS_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
+  }
+  int it = 0;
+  double r0 = -1.0, rel = 0.0;
+  double best = 1e300;
+  int best_it = 0;
+  bool done = false;
+  while (!done && it < p->d.max_iter) {
+    const int m = std::min(p->d.check_every, p->d.max_iter - it);
+    // full blocks replay a graph; with profiling the last iteration runs outside it
+    const int ng = (m == p->d.check_every) ? (p->profiling ? m - 1 : m) : 0;
+    bool used = false;
+    if (ng > 1) rc = graph_block(p, a, ng, used);
+    if (!rc) rc = launch_range(p, a, used ? ng : 0, m, m);
+    if (rc) break;
+    cudaError_t e = cudaMemcpyAsync(p->hist_host, p->hist, m * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) {
+      rc = fail(CBS_ERR_CUDA, "iteration block failed: %s", cudaGetErrorString(e));
+      break;
+    }
+    rc = collect_pass_times(p);
+    if (rc) break;
+    for (int k = 0; k < m; ++k) {
+      ++it;
+      const double r = std::sqrt(p->hist_host[k]);
+      if (r0 < 0) r0 = r;
+      rel = r0 > 0 ? r / r0 : 0.0;
+      if (!std::isfinite(r) || rel > 1e4) {
+        rc = fail(CBS_ERR_DIVERGED, "series diverged at iteration %d (relative residual %g)", it, rel);
+        done = true;
+        break;
+      }
+      // a converged iteration inside a block still lets the block finish: `it` counts
+      // every iteration that ran and `rel` is the residual of the last one
+      if (p->d.tol > 0 && rel <= p->d.tol) done = true;
+      if (rel < 0.99 * best) {
+        best = rel;
+        best_it = it;
+      }
+    }
+    // stagnation: the residual has sat at its rounding floor for a long stretch
+    if (!done && !rc && p->d.tol > 0 && it - best_it >= std::max(1000, it / 4)) {
+      rc = fail(CBS_ERR_STAGNATED, "residual stagnated at %g (best %g) after %d iterations, above tol %g",
+                rel, best, it, p->d.tol);
+      done = true;
+    }
+  }
+  S->iters = it;
+  S->rel_resid = rel;
+  S->resid0 = r0 < 0 ? 0.0 : r0;
+  if (rc == CBS_OK && p->d.tol > 0 && !(rel <= p->d.tol))
+    rc = fail(CBS_ERR_NOT_CONVERGED, "relative residual %g > tol %g after %d iterations", rel, p->d.tol, it);
+  S->status = rc;
+  S->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* cbs_last_error(void) { return g_err.c_str(); }
+
+int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
+  g_err.clear();
+  if (!out || !desc) return fail(CBS_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  const cbs_plan_desc& d = *desc;
+  const int dims[3] = {d.nx, d.ny, d.nz};
+  for (int a = 0; a < 3; ++a) {
+    if (dims[a] < 1 || dims[a] > kMaxN) return fail(CBS_ERR_ARG, "axis %d size %d outside [1, %d]", a, dims[a], kMaxN);
+    if (d.pad_lo[a] < 0 || d.pad_hi[a] < 0 || 2 * d.pad_lo[a] > dims[a] || 2 * d.pad_hi[a] > dims[a] ||
+        d.pad_lo[a] + d.pad_hi[a] >= dims[a])
+      return fail(CBS_ERR_ARG, "axis %d pads (%d, %d) do not fit size %d", a, d.pad_lo[a], d.pad_hi[a], dims[a]);
+  }
+  if (!(d.pitch_m > 0) || !(d.lambda_m > 0) || !(d.n_bg > 0))
+    return fail(CBS_ERR_ARG, "pitch, wavelength and n_bg must be positive");
+  if (d.max_iter < 1 || d.check_every < 1) return fail(CBS_ERR_ARG, "max_iter and check_every must be >= 1");
+  AxisPlan ax, ay, az;
+  if (!factor_axis(d.nx, 16, ax)) return fail(CBS_ERR_ARG, "nx = %d is not a product of 2,3,5,7,11,13", d.nx);
+  if (!factor_axis(d.ny, 16, ay)) return fail(CBS_ERR_ARG, "ny = %d is not a product of 2,3,5,7,11,13", d.ny);
+  if (!factor_axis(d.nz, 16, az)) return fail(CBS_ERR_ARG, "nz = %d is not a product of 2,3,5,7,11,13", d.nz);
+  if (ax.T > 512 || ay.T > 512 || az.T > 512)
+    return fail(CBS_ERR_ARG, "an axis needs more than 512 threads per transform (unsupported factorisation)");
+
+  cbs_plan_s* p = new cbs_plan_s();
+  p->d = d;
+  p->N = (size_t)d.nx * d.ny * d.nz;
+  p->pitch = d.pitch_m;
+  p->kvac = 2.0 * kPiD / d.lambda_m;
+  p->user_stream = static_cast<cudaStream_t>(d.cuda_stream);
+  auto bail = [&](int code) {
+    cbs_destroy(p);
+    return code;
+  };
+#define CKP(call)                                                                                \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) {                                                                     \
+      int code_ = (e_ == cudaErrorMemoryAllocation) ? CBS_ERR_OOM : CBS_ERR_CUDA;                \
+      fail(code_, "%s failed: %s", #call, cudaGetErrorString(e_));                               \
+      return bail(code_);                                                                        \
+    }                                                                                            \
+  } while (0)
+  CKP(cudaGetDevice(&p->device));
+  if (p->user_stream) {
+    p->stream = p->user_stream;   // work (and graph capture) on the caller's stream
+  } else {
+    CKP(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking));
+    p->own_stream = true;         // the legacy stream cannot be captured
+  }
+  CKP(cudaEventCreateWithFlags(&p->ev, cudaEventDisableTiming));
+  CKP(xpass_set_smem_limit(200 * 1024));
+  CKP(yzpass_set_smem_limit(200 * 1024));
+
+  IterArgs& a = p->base;
+  a.nx = d.nx;
+  a.ny = d.ny;
+  a.nz = d.nz;
+  a.N = p->N;
+  a.ax = ax;
+  a.ay = ay;
+  a.az = az;
+  // launch shapes: ~256 threads per x-pass block; up to 512 threads and 96 KB per y/z block
+  a.rpb = std::max(1, 256 / ax.T);   // x pass: threads = rpb * T <= 512
+  while (a.rpb > 1 && (size_t)a.rpb * 3 * d.nx * sizeof(float2) > 96 * 1024) a.rpb /= 2;
+  a.tx_y = std::min(32, pow2_ceil(d.nx));
+  while (a.tx_y > 1 && a.tx_y * ay.T > 512) a.tx_y /= 2;
+  a.tx_z = std::min(32, pow2_ceil(d.nx));
+  while (a.tx_z > 1 && (a.tx_z * az.T > 512 || (size_t)3 * d.nz * a.tx_z * sizeof(float2) > 96 * 1024)) a.tx_z /= 2;
+  if (a.rpb * ax.T > 1024 || a.tx_y * ay.T > 1024 || a.tx_z * az.T > 1024) {
+    fail(CBS_ERR_ARG, "transform too long for one block");
+    return bail(CBS_ERR_ARG);
+  }
+
+  const size_t N = p->N;
+  CKP(cudaMalloc(&p->V, N * sizeof(float2)));
+  CKP(cudaMalloc(&p->W, 3 * N * sizeof(float2)));
+  CKP(cudaMalloc(&p->tw, (size_t)(d.nx + d.ny + d.nz) * sizeof(float2)));
+  const int xb = xpass_blocks(a);
+  CKP(cudaMalloc(&p->partials, (size_t)xb * sizeof(double)));
+  CKP(cudaMalloc(&p->counter, sizeof(unsigned)));
+  CKP(cudaMemset(p->counter, 0, sizeof(unsigned)));
+  CKP(cudaMalloc(&p->hist, (size_t)d.check_every * sizeof(double)));
+  CKP(cudaMallocHost(&p->hist_host, (size_t)d.check_every * sizeof(double)));
+  CKP(cudaMalloc(&p->adj_amp, 3 * sizeof(float2)));
+  CKP(cudaMalloc(&p->dobj, sizeof(double)));
+  CKP(cudaMalloc(&p->sx, d.nx * sizeof(double)));
+  CKP(cudaMalloc(&p->sy, d.ny * sizeof(double)));
+  CKP(cudaMalloc(&p->sz, d.nz * sizeof(double)));
+  p->red_blocks = 152 * 4;
+  CKP(cudaMalloc(&p->pmin, p->red_blocks * sizeof(float)));
+  CKP(cudaMalloc(&p->pmax, p->red_blocks * sizeof(float)));
+  CKP(cudaMalloc(&p->pbad, p->red_blocks * sizeof(int)));
+  CKP(cudaMalloc(&p->pdev, p->red_blocks * sizeof(double)));
+
+  // twiddles exp(-2 pi i m / n) in FP64, rounded to FP32
+  std::vector<float2> tw;
+  for (int a2 = 0; a2 < 3; ++a2) {
+    const int n = dims[a2];
+    for (int m = 0; m < n; ++m) {
+      const double ang = -2.0 * kPiD * (double)m / (double)n;
+      tw.push_back(make_float2((float)std::cos(ang), (float)std::sin(ang)));
+    }
+  }
+  CKP(cudaMemcpy(p->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  CKP(cudaMalloc(&p->stages, 3 * kMaxStages * sizeof(int4)));
+  {
+    std::vector<int4> all;
+    for (const AxisPlan* ap : {&a.ax, &a.ay, &a.az}) {
+      std::vector<int4> t = stage_table(*ap);
+      all.insert(all.end(), t.begin(), t.end());
+    }
+    CKP(cudaMemcpy(p->stages, all.data(), all.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    a.ax.st = p->stages;
+    a.ay.st = p->stages + kMaxStages;
+    a.az.st = p->stages + 2 * kMaxStages;
+  }
+  a.twx = p->tw;
+  a.twy = p->tw + d.nx;
+  a.twz = p->tw + d.nx + d.ny;
+
+  // absorbing layers: sigma = sigma_max (t / L)^2 at depth t voxels into a layer of L voxels,
+  // sigma_max = 3 n_bg ln(1e4) / (k_vac L pitch) (round-trip amplitude 1e-4), summed over axes
+  for (int a2 = 0; a2 < 3; ++a2) {
+    const int n = dims[a2], lo = d.pad_lo[a2], hi = d.pad_hi[a2];
+    std::vector<double> s(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+      if (i < lo) {
+        const double smax = 3.0 * d.n_bg * std::log(1.0e4) / (p->kvac * lo * d.pitch_m);
+        const double t = (double)(lo - i) / lo;
+        s[i] = smax * t * t;
+      } else if (i >= n - hi) {
+        const double smax = 3.0 * d.n_bg * std::log(1.0e4) / (p->kvac * hi * d.pitch_m);
+        const double t = (double)(i - (n - hi - 1)) / hi;
+        s[i] = smax * t * t;
+      }
+    }
+    double* dst = a2 == 0 ? p->sx : (a2 == 1 ? p->sy : p->sz);
+    CKP(cudaMemcpy(dst, s.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+  }
+
+  a.W = p->W;
+  a.V = p->V;
+  a.partials = p->partials;
+  a.counter = p->counter;
+  a.hist = p->hist;
+  a.invN = (float)(1.0 / (double)N);
+#undef CKP
+  *out = p;
+  return CBS_OK;
+}
+
+void cbs_destroy(cbs_plan_t p) {
+  if (!p) return;
+  cudaSetDevice(p->device);
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  drop_graphs(p);
+  void* devs[] = {p->V, p->W, p->tw, p->stages, p->partials, p->counter, p->hist, p->adj_amp, p->dobj,
+                  p->sx, p->sy, p->sz, p->pmin, p->pmax, p->pbad, p->pdev, p->eps_dev,
+                  p->Ef, p->Ea, p->grad_dev};
+  for (void* q : devs)
+    if (q) cudaFree(q);
+  if (p->hist_host) cudaFreeHost(p->hist_host);
+  if (p->ev) cudaEventDestroy(p->ev);
+  for (cudaEvent_t e : p->pev)
+    if (e) cudaEventDestroy(e);
+  if (p->stream && p->own_stream) cudaStreamDestroy(p->stream);
+  delete p;
+}
+
+int cbs_set_profiling(cbs_plan_t p, int on) {
+  g_err.clear();
+  if (!p) return fail(CBS_ERR_ARG, "NULL plan");
+  CK(cudaSetDevice(p->device));
+  if (on && !p->pev[0])
+    for (cudaEvent_t& e : p->pev) CK(cudaEventCreate(&e));
+  if ((on != 0) != p->profiling) {
+    CK(cudaStreamSynchronize(p->stream));
+    drop_graphs(p);
+  }
+  p->profiling = on != 0;
+  return CBS_OK;
+}
+
+int cbs_pass_times(cbs_plan_t p, double ms_total[5], long long launches[5], int reset) {
+  g_err.clear();
+  if (!p) return fail(CBS_ERR_ARG, "NULL plan");
+  for (int i = 0; i < 5; ++i) {
+    if (ms_total) ms_total[i] = p->pass_ms[i];
+    if (launches) launches[i] = p->pass_n[i];
+    if (reset) {
+      p->pass_ms[i] = 0.0;
+      p->pass_n[i] = 0;
+    }
+  }
+  return CBS_OK;
+}
+
+int cbs_set_solver(cbs_plan_t p, double tol, int max_iter, int check_every) {
+  g_err.clear();
+  if (!p) return fail(CBS_ERR_ARG, "NULL plan");
+  if (max_iter < 1 || check_every < 1) return fail(CBS_ERR_ARG, "max_iter and check_every must be >= 1");
+  if (check_every != p->d.check_every) {
+    CK(cudaSetDevice(p->device));
+    CK(cudaStreamSynchronize(p->stream));
+    drop_graphs(p);
+    double* h = nullptr;
+    double* hh = nullptr;
+    CK(cudaMalloc(&h, (size_t)check_every * sizeof(double)));
+    cudaError_t e = cudaMallocHost(&hh, (size_t)check_every * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaFree(h);
+      return fail(CBS_ERR_CUDA, "cudaMallocHost: %s", cudaGetErrorString(e));
+    }
+    cudaFree(p->hist);
+    cudaFreeHost(p->hist_host);
+    p->hist = h;
+    p->hist_host = hh;
+    p->base.hist = h;
+  }
+  p->d.tol = tol;
+  p->d.max_iter = max_iter;
+  p->d.check_every = check_every;
+  return CBS_OK;
+}
+
+int cbs_set_permittivity(cbs_plan_t p, const float* eps) {
+  g_err.clear();
+  if (!p || !eps) return fail(CBS_ERR_ARG, "NULL argument");
+  int rc = sync_in(p);
+  if (rc) return rc;
+  const int B = p->red_blocks;
+  CK(launch_eps_minmax(eps, p->N, p->pmin, p->pmax, p->pbad, B, p->stream));
+  std::vector<float> mn(B), mx(B);
+  std::vector<int> bad(B);
+  CK(cudaMemcpyAsync(mn.data(), p->pmin, B * sizeof(float), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaMemcpyAsync(mx.data(), p->pmax, B * sizeof(float), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaMemcpyAsync(bad.data(), p->pbad, B * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  double lo = 1e300, hi = -1e300;
+  for (int b = 0; b < B; ++b) {
+    if (bad[b]) return fail(CBS_ERR_ARG, "permittivity contains a non-finite value");
+    lo = std::min(lo, (double)mn[b]);
+    hi = std::max(hi, (double)mx[b]);
+  }
+  const double kv2 = (p->kvac * p->pitch) * (p->kvac * p->pitch);
+  const double k0sq = 0.5 * kv2 * (lo + hi);
+  CK(launch_k2_maxdev(eps, p->d.nx, p->d.ny, p->d.nz, p->sx, p->sy, p->sz, kv2, k0sq, p->pdev, B, p->stream));
+  std::vector<double> dv(B);
+  CK(cudaMemcpyAsync(dv.data(), p->pdev, B * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  double epsilon = 0.0;
+  for (int b = 0; b < B; ++b) epsilon = std::max(epsilon, dv[b]);
+  if (!(epsilon > 0.0) || !std::isfinite(epsilon))
+    return fail(CBS_ERR_ARG, "epsilon = %g: a lossless homogeneous grid has no convergent splitting", epsilon);
+  CK(launch_build_v(eps, p->d.nx, p->d.ny, p->d.nz, p->sx, p->sy, p->sz, kv2, k0sq, epsilon, p->V, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  p->k0sq_s = k0sq;
+  p->eps_s = epsilon;
+  IterArgs& a = p->base;
+  a.inv_eps = (float)(1.0 / epsilon);
+  a.kt2 = make_float2((float)k0sq, (float)epsilon);
+  p->have_eps = true;
+  drop_graphs(p);   // kernel parameters changed
+  return CBS_OK;
+}
+
+int cbs_get_splitting(cbs_plan_t p, double* k0sq, double* epsilon) {
+  g_err.clear();
+  if (!p) return fail(CBS_ERR_ARG, "NULL plan");
+  if (!p->have_eps) return fail(CBS_ERR_STATE, "cbs_set_permittivity has not been called");
+  const double s = 1.0 / (p->pitch * p->pitch);
+  if (k0sq) *k0sq = p->k0sq_s * s;
+  if (epsilon) *epsilon = p->eps_s * s;
+  return CBS_OK;
+}
+
+int cbs_forward(cbs_plan_t p, const cbs_source* src, void* E_dev, cbs_stats* stats) {
+  g_err.clear();
+  if (stats) *stats = cbs_stats{};
+  if (!p || !src || !E_dev) {
+    if (stats) stats->status = CBS_ERR_ARG;
+    return fail(CBS_ERR_ARG, "NULL argument");
+  }
+  SourceArgs s;
+  int rc = make_source(p, src, s);
+  if (!rc) rc = sync_in(p);
+  if (rc) {
+    if (stats) stats->status = rc;
+    return rc;
+  }
+  return run_series(p, static_cast<float2*>(E_dev), s, src->warm_start != 0, stats);
+}
+
+int cbs_adjoint(cbs_plan_t p, const int r0[3], const void* E_dev, void* Eadj_dev, cbs_stats* stats) {
+  g_err.clear();
+  if (stats) *stats = cbs_stats{};
+  if (!p || !r0 || !E_dev || !Eadj_dev) {
+    if (stats) stats->status = CBS_ERR_ARG;
+    return fail(CBS_ERR_ARG, "NULL argument");
+  }
+  if (r0[0] < 0 || r0[0] >= p->d.nx || r0[1] < 0 || r0[1] >= p->d.ny || r0[2] < 0 || r0[2] >= p->d.nz) {
+    if (stats) stats->status = CBS_ERR_ARG;
+    return fail(CBS_ERR_ARG, "r0 (%d,%d,%d) outside the grid", r0[0], r0[1], r0[2]);
+  }
+  int rc = sync_in(p);
+  if (rc) return rc;
+  CK(launch_adjoint_amp(static_cast<const float2*>(E_dev), p->N, p->d.nx, p->d.ny, r0[0], r0[1], r0[2],
+                        (float)(p->pitch * p->pitch), p->adj_amp, p->stream));
+  SourceArgs s{};
+  s.kind = CBS_SRC_POINT;
+  s.px = r0[0];
+  s.py = r0[1];
+  s.pz = r0[2];
+  s.amp_dev = p->adj_amp;
+  return run_series(p, static_cast<float2*>(Eadj_dev), s, false, stats);
+}
+
+int cbs_gradient(cbs_plan_t p, const void* E_dev, const void* Eadj_dev, const int r0[3], float* grad_dev,
+                 double* objective) {
+  g_err.clear();
+  if (!p || !E_dev || !Eadj_dev || !grad_dev) return fail(CBS_ERR_ARG, "NULL argument");
+  int rc = sync_in(p);
+  if (rc) return rc;
+  const float coef = (float)(2.0 * p->kvac * p->kvac);
+  CK(launch_gradient(static_cast<const float2*>(E_dev), static_cast<const float2*>(Eadj_dev), p->N, coef,
+                     grad_dev, p->stream));
+  if (r0 && objective) {
+    if (r0[0] < 0 || r0[0] >= p->d.nx || r0[1] < 0 || r0[1] >= p->d.ny || r0[2] < 0 || r0[2] >= p->d.nz)
+      return fail(CBS_ERR_ARG, "r0 (%d,%d,%d) outside the grid", r0[0], r0[1], r0[2]);
+    CK(launch_objective(static_cast<const float2*>(E_dev), p->N, p->d.nx, p->d.ny, r0[0], r0[1], r0[2], p->dobj,
+                        p->stream));
+    CK(cudaMemcpyAsync(objective, p->dobj, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  }
+  CK(cudaStreamSynchronize(p->stream));
+  return CBS_OK;
+}
+
+int cbs_design_step_host(cbs_plan_t p, const float* eps_host, const cbs_source* src, const int r0[3],
+                         float* grad_host, double* objective, cbs_stats* fwd, cbs_stats* adj) {
+  g_err.clear();
+  if (!p || !eps_host || !src || !r0 || !grad_host || !objective) return fail(CBS_ERR_ARG, "NULL argument");
+  CK(cudaSetDevice(p->device));
+  const size_t N = p->N;
+  if (!p->eps_dev) {
+    CK(cudaMalloc(&p->eps_dev, N * sizeof(float)));
+    CK(cudaMalloc(&p->grad_dev, N * sizeof(float)));
+    CK(cudaMalloc(&p->Ef, 3 * N * sizeof(float2)));
+    CK(cudaMalloc(&p->Ea, 3 * N * sizeof(float2)));
+  }
+  int rc = sync_in(p);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(p->eps_dev, eps_host, N * sizeof(float), cudaMemcpyHostToDevice, p->stream));
+  rc = cbs_set_permittivity(p, p->eps_dev);
+  if (rc) return rc;
+  cbs_source s = *src;
+  s.warm_start = 0;
+  rc = cbs_forward(p, &s, p->Ef, fwd);
+  if (rc) return rc;
+  rc = cbs_adjoint(p, r0, p->Ef, p->Ea, adj);
+  if (rc) return rc;
+  rc = cbs_gradient(p, p->Ef, p->Ea, r0, p->grad_dev, objective);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(grad_host, p->grad_dev, N * sizeof(float), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return CBS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,88 @@
+// cbs_internal.h -- structures shared by the host library and the CUDA kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+
+namespace cbs {
+
+constexpr int kMaxStages = 8;
+
+// Stockham radix plan of one axis: n = r[0] * r[1] * ... * r[ns-1]; a transform is run
+// by T = n / min(r) threads, each doing at most one radix-r butterfly per stage.  Per stage
+// q: Ns[q] = r[0] * ... * r[q-1], stride[q] = n / r[q] (butterflies, and the distance
+// between a butterfly's inputs), twstep[q] = n / (Ns[q] r[q]).
+// The per-stage table lives in device memory as int4 {r, Ns, stride, twstep} and is read
+// with uniform loads (a dynamically indexed kernel-parameter array would be copied to the
+// stack).
+struct AxisPlan {
+  int n;
+  int ns;
+  int T;
+  const int4* st;         // device table, ns entries
+  int r[kMaxStages];      // host copy of the radices
+};
+
+// Source term in the scaled units of the kernels (all k^2 quantities times pitch^2).
+struct SourceArgs {
+  int kind;               // 0 plane wave, 1 point, 2 user array
+  float2 amp[3];          // plane wave: pol * (-2 i k_b pitch); point: pol * pitch^2
+  int zp;                 // plane-wave sheet
+  int px, py, pz;         // point-source voxel
+  const float2* amp_dev;  // point source with amplitudes on the device (adjoint), or null
+  const float2* user;     // user S [3][N]
+  float user_scale;       // pitch^2
+};
+
+// Everything one CBS iteration needs (kernel parameters, by value).
+struct IterArgs {
+  int nx, ny, nz;
+  size_t N;
+  AxisPlan ax, ay, az;
+  const float2* twx;      // exp(-2 pi i m / n), m < n, per axis
+  const float2* twy;
+  const float2* twz;
+  float2* E;              // field [3][N]
+  float2* W;              // workspace [3][N]
+  const float2* V;        // potential [N], scaled
+  SourceArgs src;
+  float inv_eps;          // 1 / epsilon (scaled)
+  float2 kt2;             // k0^2 + i epsilon (scaled)
+  float invN;             // 1 / N, folded into the k-space multiply
+  double* partials;       // per-block residual partial sums
+  unsigned* counter;      // last-block-done counter (left at 0)
+  double* hist;           // hist[slot] = sum |delta|^2 of this iteration
+  int slot;
+  // launch shapes
+  int rpb;                // rows per block, x passes
+  int tx_y, tx_z;         // x-columns per block, y and z passes
+};
+
+// Launchers (one per pass of an iteration); each returns the launch error.
+cudaError_t launch_xpass_fwd(const IterArgs& a, cudaStream_t s);   // W = FFTx(V E + S)
+cudaError_t launch_ypass(const IterArgs& a, bool inverse, cudaStream_t s);
+cudaError_t launch_zpass_green(const IterArgs& a, cudaStream_t s); // FFTz, G(p), IFFTz
+cudaError_t launch_xpass_inv_update(const IterArgs& a, cudaStream_t s);  // IFFTx, update, residual
+
+// Shared-memory bytes and threads of each pass for the plan's shapes.
+size_t xpass_smem(const IterArgs& a);
+size_t ypass_smem(const IterArgs& a);
+size_t zpass_smem(const IterArgs& a);
+int xpass_blocks(const IterArgs& a);
+
+// Set-up and gradient kernels (cbs_misc.cu).
+cudaError_t launch_eps_minmax(const float* eps, size_t N, float* part_min, float* part_max,
+                              int* part_bad, int blocks, cudaStream_t s);
+cudaError_t launch_k2_maxdev(const float* eps, int nx, int ny, int nz, const double* sx,
+                             const double* sy, const double* sz, double kv2, double k0sq,
+                             double* part, int blocks, cudaStream_t s);
+cudaError_t launch_build_v(const float* eps, int nx, int ny, int nz, const double* sx,
+                           const double* sy, const double* sz, double kv2, double k0sq,
+                           double eps_shift, float2* V, cudaStream_t s);
+cudaError_t launch_adjoint_amp(const float2* E, size_t N, int nx, int ny, int x, int y, int z,
+                               float scale, float2* amp, cudaStream_t s);
+cudaError_t launch_gradient(const float2* E, const float2* Ea, size_t N, float coef, float* g,
+                            cudaStream_t s);
+cudaError_t launch_objective(const float2* E, size_t N, int nx, int ny, int x, int y, int z,
+                             double* out, cudaStream_t s);
+
+}  // namespace cbs

@@ -1,0 +1,76 @@
+"""The C ABI without a GPU: the library builds for sm_103a, loads, exports every function
+include/cbs.h declares, and the ctypes structures match the C layout (checked with gcc)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import subprocess
+
+from paper_2506_15411_gb300 import _lib as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "cbs.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(cbs_\w+)\s*\(", text, re.M)))
+
+
+def test_header_and_binding_agree():
+    assert declared_functions() == sorted(L.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(built_lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", built_lib], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(cbs_\w+)", out))
+    missing = set(declared_functions()) - exported
+    assert not missing, missing
+    lib = L.load(built_lib)
+    for name in declared_functions():
+        assert hasattr(lib, name)
+    assert lib.cbs_last_error() == b""
+
+
+def test_struct_layout_matches_c(tmp_path, built_lib):
+    src = tmp_path / "layout.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "cbs.h"
+#define F(T, m) printf(#T " " #m " %zu\n", offsetof(T, m))
+int main(void) {
+  printf("cbs_plan_desc size %zu\n", sizeof(cbs_plan_desc));
+  printf("cbs_source size %zu\n", sizeof(cbs_source));
+  printf("cbs_stats size %zu\n", sizeof(cbs_stats));
+  F(cbs_plan_desc, pitch_m); F(cbs_plan_desc, pad_lo); F(cbs_plan_desc, pad_hi); F(cbs_plan_desc, tol);
+  F(cbs_plan_desc, max_iter); F(cbs_plan_desc, check_every); F(cbs_plan_desc, cuda_stream);
+  F(cbs_source, pol); F(cbs_source, z_plane); F(cbs_source, r0); F(cbs_source, user_src_dev);
+  F(cbs_source, warm_start);
+  F(cbs_stats, rel_resid); F(cbs_stats, resid0); F(cbs_stats, seconds); F(cbs_stats, status);
+  return 0;
+}
+''')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for ln in lines:
+        if ln:
+            t, m, v = ln.split()
+            got[(t, m)] = int(v)
+    types = {"cbs_plan_desc": L.cbs_plan_desc, "cbs_source": L.cbs_source, "cbs_stats": L.cbs_stats}
+    for (t, m), v in got.items():
+        if m == "size":
+            assert ctypes.sizeof(types[t]) == v, (t, v)
+        else:
+            assert getattr(types[t], m).offset == v, (t, m, v)
+
+
+def test_return_codes_match_header():
+    text = open(HEADER).read()
+    for name in ("CBS_OK", "CBS_ERR_ARG", "CBS_ERR_OOM", "CBS_ERR_NOT_CONVERGED", "CBS_ERR_DIVERGED",
+                 "CBS_ERR_CUDA", "CBS_ERR_STATE", "CBS_ERR_STAGNATED", "CBS_SRC_PLANE_WAVE", "CBS_SRC_POINT", "CBS_SRC_USER"):
+        m = re.search(r"#define\s+%s\s+\(?(-?\d+)\)?" % name, text)
+        assert m and int(m.group(1)) == getattr(L, name), name
