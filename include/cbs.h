@@ -148,6 +148,24 @@ int cbs_design_step_host(cbs_plan_t plan, const float* eps_host, const cbs_sourc
 int cbs_set_profiling(cbs_plan_t plan, int on);
 int cbs_pass_times(cbs_plan_t plan, double ms_total[5], long long launches[5], int reset);
 
+/* The splitting of a permittivity grid (what cbs_set_permittivity computes: k0^2 and
+ * epsilon in SI units [1/m^2]) without a plan and without allocating any memory.  For
+ * callers that cannot call cudaMalloc: code whose device memory is all handed out by another
+ * allocator, or loops that must not pay for, or synchronise the device on, cudaMalloc and
+ * cudaFree.  The paper has no counterpart; it is a service of this library.
+ *   desc: nx, ny, nz, pitch_m, lambda_m, n_bg, pad_lo, pad_hi and cuda_stream are used (the
+ *         kernels run on cuda_stream; NULL is the legacy stream); the solver fields are not.
+ *   eps_real_dev: float32 [nz][ny][nx] on the current device, layers included.
+ * Scratch: one ~80 KB array in device memory per device that loads the library, kept until
+ * the process exits.  The first call on a device looks up its address (do that first call
+ * before any stream capture).  Every call shares the array and leaves its contents behind;
+ * calls that overlap on the GPU (other streams or threads) race and give wrong results.
+ * Limit: nx * ny * nz <= 268,435,456 voxels (4096 blocks of 65,536); larger grids return
+ * CBS_ERR_ARG.  Other errors: CBS_ERR_ARG (NULL, bad dims or pads, non-finite eps,
+ * epsilon = 0), CBS_ERR_CUDA.  Blocks the host until the result is back. */
+int cbs_splitting_noalloc(const cbs_plan_desc* desc, const float* eps_real_dev, double* k0sq,
+                          double* epsilon);
+
 /* Free the plan and its device memory (NULL is a no-op). */
 void cbs_destroy(cbs_plan_t plan);
 

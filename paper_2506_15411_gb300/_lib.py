@@ -28,7 +28,8 @@ CBS_SRC_USER = 2
 # Every symbol include/cbs.h declares.
 EXPORTS = ("cbs_plan", "cbs_set_permittivity", "cbs_get_splitting", "cbs_set_solver",
            "cbs_forward", "cbs_adjoint", "cbs_gradient", "cbs_design_step_host",
-           "cbs_set_profiling", "cbs_pass_times", "cbs_destroy", "cbs_last_error")
+           "cbs_set_profiling", "cbs_pass_times", "cbs_splitting_noalloc", "cbs_destroy",
+           "cbs_last_error")
 
 PASS_NAMES = ("k_xpass_fwd", "k_ypass_fwd", "k_zpass_green", "k_ypass_inv", "k_xpass_inv_update")
 
@@ -74,6 +75,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                          POINTER(c_double), POINTER(cbs_stats), POINTER(cbs_stats)]),
         "cbs_set_profiling": (c_int, [P, c_int]),
         "cbs_pass_times": (c_int, [P, POINTER(c_double * 5), POINTER(ctypes.c_longlong * 5), c_int]),
+        "cbs_splitting_noalloc": (c_int, [POINTER(cbs_plan_desc), P, POINTER(c_double), POINTER(c_double)]),
         "cbs_destroy": (None, [P]),
         "cbs_last_error": (ctypes.c_char_p, []),
     }

@@ -139,6 +139,14 @@ bool same_source(const SourceArgs& a, const SourceArgs& b) {
 
 }  // namespace
 
+namespace cbs {
+// Message for cbs_last_error from other translation units.
+const char* set_last_error(const char* msg) {
+  g_err = msg;
+  return g_err.c_str();
+}
+}  // namespace cbs
+
 struct cbs_plan_s {
   cbs_plan_desc d{};
   int device = 0;
