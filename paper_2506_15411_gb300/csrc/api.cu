@@ -10,6 +10,8 @@
 //   5. x pass     W = IFFT_x(W); delta = gamma (E - W); E -= delta; sum |delta|^2 (FP64)
 // Every `check_every` iterations the host reads the FP64 residual sums and decides whether
 // to stop; a full block of iterations is replayed from a CUDA graph.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -19,6 +21,7 @@
 #include <cstdio>
 #include <cstring>
 #include <functional>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -102,13 +105,22 @@ bool factor_axis(int n, int max_radix, AxisPlan& out) {
   return true;
 }
 
-// Device table of an axis plan: per stage {r, Ns, n / r, n / (Ns r)}.
+int float_bits(float f) {
+  int i;
+  std::memcpy(&i, &f, sizeof(i));
+  return i;
+}
+
+// Device table of an axis plan: per stage {r, Ns, n / r, n / (Ns r)} and
+// {bits of 1 / (n / r), bits of 1 / Ns, 0, 0}.
 std::vector<int4> stage_table(const AxisPlan& ap) {
-  std::vector<int4> t(kMaxStages, make_int4(1, 1, 1, 1));
+  std::vector<int4> t(2 * kMaxStages, make_int4(1, 1, 1, 1));
   int Ns = 1;
   for (int q = 0; q < ap.ns; ++q) {
     const int r = ap.r[q];
-    t[q] = make_int4(r, Ns, ap.n / r, ap.n / (Ns * r));
+    const int stride = ap.n / r;
+    t[2 * q] = make_int4(r, Ns, stride, ap.n / (Ns * r));
+    t[2 * q + 1] = make_int4(float_bits(1.0f / (float)stride), float_bits(1.0f / (float)Ns), 0, 0);
     Ns *= r;
   }
   return t;
@@ -118,6 +130,39 @@ int pow2_ceil(int v) {
   int p = 1;
   while (p < v) p <<= 1;
   return p;
+}
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// cuTensorMapEncodeTiled from the driver, looked up once.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 4D map of the workspace W viewed as [3][nz][ny][nx] complex64 (8-byte elements) with row
+// pitch nxp; box = {bx, by, bz, 1}.  Elements beyond nx, ny or nz read as zero and are not
+// written.
+bool encode_w_map(CUtensorMap* tm, float2* W, int nx, int ny, int nz, int nxp, int bx, int by, int bz) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, 3};
+  const cuuint64_t row = (cuuint64_t)nxp * sizeof(float2);
+  const cuuint64_t strides[3] = {row, row * ny, row * ny * nz};
+  const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, W, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // A captured block of iterations bakes in the field pointer and the whole source.
@@ -154,12 +199,16 @@ struct cbs_plan_s {
   cudaStream_t stream = nullptr;   // the caller's stream, or an owned one for NULL (legacy)
   bool own_stream = false;
   cudaEvent_t ev = nullptr;
+  CUtensorMap tmy{}, tmz{};        // W maps for the y pass and the z pass
+  int* err_dev = nullptr;          // kernels' error flag
+  int* err_host = nullptr;         // pinned copy
   IterArgs base{};
   size_t N = 0;
   double pitch = 0, kvac = 0;
   // device memory owned by the plan
   float2* V = nullptr;
   float2* W = nullptr;
+  float2* Ei = nullptr;            // the field being iterated, padded rows
   float2* tw = nullptr;
   int4* stages = nullptr;
   double* partials = nullptr;
@@ -209,15 +258,15 @@ int sync_in(cbs_plan_s* p) {
 }
 
 // The five launches of one iteration; with ev != null, events ev[0..5] bracket them.
-int launch_iteration(const IterArgs& a, cudaStream_t s, cudaEvent_t* ev) {
+int launch_iteration(const cbs_plan_s* p, const IterArgs& a, cudaStream_t s, cudaEvent_t* ev) {
   if (ev) CK(cudaEventRecord(ev[0], s));
   CK(launch_xpass_fwd(a, s));
   if (ev) CK(cudaEventRecord(ev[1], s));
-  CK(launch_ypass(a, false, s));
+  CK(launch_ypass(p->tmy, a, false, s));
   if (ev) CK(cudaEventRecord(ev[2], s));
-  CK(launch_zpass_green(a, s));
+  CK(launch_zpass_green(p->tmz, a, s));
   if (ev) CK(cudaEventRecord(ev[3], s));
-  CK(launch_ypass(a, true, s));
+  CK(launch_ypass(p->tmy, a, true, s));
   if (ev) CK(cudaEventRecord(ev[4], s));
   CK(launch_xpass_inv_update(a, s));
   if (ev) CK(cudaEventRecord(ev[5], s));
@@ -230,7 +279,7 @@ int launch_range(cbs_plan_s* p, const IterArgs& a0, int k0, int k1, int m) {
   IterArgs a = a0;
   for (int k = k0; k < k1; ++k) {
     a.slot = k;
-    int rc = launch_iteration(a, p->stream, (p->profiling && k == m - 1) ? p->pev : nullptr);
+    int rc = launch_iteration(p, a, p->stream, (p->profiling && k == m - 1) ? p->pev : nullptr);
     if (rc) return rc;
   }
   return CBS_OK;
@@ -320,12 +369,16 @@ int run_series(cbs_plan_s* p, float2* E, const SourceArgs& src, bool warm, cbs_s
   *S = cbs_stats{};
   if (!p->have_eps) return S->status = fail(CBS_ERR_STATE, "cbs_set_permittivity has not been called");
   IterArgs a = p->base;
-  a.E = E;
+  a.E = p->Ei;   // iterate on the plan's padded copy; the caller's E is read and written once
   a.src = src;
   int rc = CBS_OK;
-  if (!warm) {
-    cudaError_t e = cudaMemsetAsync(E, 0, 3 * p->N * sizeof(float2), p->stream);
-    if (e != cudaSuccess) return S->status = fail(CBS_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
+  const size_t dense_row = (size_t)p->d.nx * sizeof(float2), pad_row = (size_t)a.nxp * sizeof(float2);
+  const size_t rows = (size_t)3 * p->d.ny * p->d.nz;
+  {
+    cudaError_t e = cudaMemsetAsync(p->Ei, 0, 3 * a.Nw * sizeof(float2), p->stream);
+    if (e == cudaSuccess && warm)
+      e = cudaMemcpy2DAsync(p->Ei, pad_row, E, dense_row, dense_row, rows, cudaMemcpyDeviceToDevice, p->stream);
+    if (e != cudaSuccess) return S->status = fail(CBS_ERR_CUDA, "field copy-in: %s", cudaGetErrorString(e));
   }
   int it = 0;
   double r0 = -1.0, rel = 0.0;
@@ -341,9 +394,14 @@ int run_series(cbs_plan_s* p, float2* E, const SourceArgs& src, bool warm, cbs_s
     if (!rc) rc = launch_range(p, a, used ? ng : 0, m, m);
     if (rc) break;
     cudaError_t e = cudaMemcpyAsync(p->hist_host, p->hist, m * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->err_host, p->err_dev, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) {
       rc = fail(CBS_ERR_CUDA, "iteration block failed: %s", cudaGetErrorString(e));
+      break;
+    }
+    if (*p->err_host) {
+      rc = fail(CBS_ERR_CUDA, "a tensor-copy wait timed out in an FFT pass (device error %d)", *p->err_host);
       break;
     }
     rc = collect_pass_times(p);
@@ -372,6 +430,12 @@ int run_series(cbs_plan_s* p, float2* E, const SourceArgs& src, bool warm, cbs_s
                 rel, best, it, p->d.tol);
       done = true;
     }
+  }
+  {
+    cudaError_t e = cudaMemcpy2DAsync(E, dense_row, p->Ei, pad_row, dense_row, rows, cudaMemcpyDeviceToDevice,
+                                      p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess && rc == CBS_OK) rc = fail(CBS_ERR_CUDA, "field copy-out: %s", cudaGetErrorString(e));
   }
   S->iters = it;
   S->rel_resid = rel;
@@ -449,21 +513,39 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
   a.ax = ax;
   a.ay = ay;
   a.az = az;
-  // launch shapes: ~256 threads per x-pass block; up to 512 threads and 96 KB per y/z block
-  a.rpb = std::max(1, 256 / ax.T);   // x pass: threads = rpb * T <= 512
-  while (a.rpb > 1 && (size_t)a.rpb * 3 * d.nx * sizeof(float2) > 96 * 1024) a.rpb /= 2;
-  a.tx_y = std::min(32, pow2_ceil(d.nx));
-  while (a.tx_y > 1 && a.tx_y * ay.T > 512) a.tx_y /= 2;
-  a.tx_z = std::min(32, pow2_ceil(d.nx));
-  while (a.tx_z > 1 && (a.tx_z * az.T > 512 || (size_t)3 * d.nz * a.tx_z * sizeof(float2) > 96 * 1024)) a.tx_z /= 2;
-  if (a.rpb * ax.T > 1024 || a.tx_y * ay.T > 1024 || a.tx_z * az.T > 1024) {
-    fail(CBS_ERR_ARG, "transform too long for one block");
+  // launch shapes: ~256 threads per x-pass block; y and z tiles of TX columns by whole
+  // tensor-copy boxes, TX as wide as fits 2 blocks per SM (<= 113 KB of shared memory)
+  a.nxp = round_up(d.nx, 16);
+  a.rpb = std::max(1, std::min(64, (int)((100 * 1024 - 272) / (80 * a.nxp))));   // x tile <= 100 KB
+  a.Nw = (size_t)a.nxp * d.ny * d.nz;
+  a.yb = std::min(kBoxRows, round_up(d.ny, 4));
+  a.zb = std::min(kBoxRows, round_up(d.nz, 4));
+  a.nyr = round_up(d.ny, a.yb);
+  a.nzr = round_up(d.nz, a.zb);
+  const size_t kTileBudget = 113 * 1024;
+  a.tx_y = 16;
+  while (a.tx_y > 4 && (size_t)(a.nyr + d.ny) * a.tx_y * sizeof(float2) > kTileBudget) a.tx_y /= 2;
+  a.tx_z = 16;
+  while (a.tx_z > 4 && (size_t)(3 * a.nzr + d.nz) * a.tx_z * sizeof(float2) > kTileBudget) a.tx_z /= 2;
+  if (xpass_smem(a) > 200 * 1024 || ypass_smem(a) > 200 * 1024 || zpass_smem(a) > 200 * 1024) {
+    fail(CBS_ERR_ARG, "axis too long for the shared-memory tiles");
     return bail(CBS_ERR_ARG);
   }
 
   const size_t N = p->N;
-  CKP(cudaMalloc(&p->V, N * sizeof(float2)));
-  CKP(cudaMalloc(&p->W, 3 * N * sizeof(float2)));
+  CKP(cudaMalloc(&p->V, a.Nw * sizeof(float2)));
+  CKP(cudaMemset(p->V, 0, a.Nw * sizeof(float2)));        // row padding stays zero
+  CKP(cudaMalloc(&p->Ei, 3 * a.Nw * sizeof(float2)));
+  CKP(cudaMalloc(&p->W, 3 * a.Nw * sizeof(float2)));
+  CKP(cudaMemset(p->W, 0, 3 * a.Nw * sizeof(float2)));   // row padding stays zero
+  CKP(cudaMalloc(&p->err_dev, sizeof(int)));
+  CKP(cudaMemset(p->err_dev, 0, sizeof(int)));
+  CKP(cudaMallocHost(&p->err_host, sizeof(int)));
+  if (!encode_w_map(&p->tmy, p->W, d.nx, d.ny, d.nz, a.nxp, a.tx_y, a.yb, 1) ||
+      !encode_w_map(&p->tmz, p->W, d.nx, d.ny, d.nz, a.nxp, a.tx_z, 1, a.zb)) {
+    fail(CBS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the workspace");
+    return bail(CBS_ERR_CUDA);
+  }
   CKP(cudaMalloc(&p->tw, (size_t)(d.nx + d.ny + d.nz) * sizeof(float2)));
   const int xb = xpass_blocks(a);
   CKP(cudaMalloc(&p->partials, (size_t)xb * sizeof(double)));
@@ -492,7 +574,7 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
     }
   }
   CKP(cudaMemcpy(p->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
-  CKP(cudaMalloc(&p->stages, 3 * kMaxStages * sizeof(int4)));
+  CKP(cudaMalloc(&p->stages, 3 * 2 * kMaxStages * sizeof(int4)));
   {
     std::vector<int4> all;
     for (const AxisPlan* ap : {&a.ax, &a.ay, &a.az}) {
@@ -501,8 +583,8 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
     }
     CKP(cudaMemcpy(p->stages, all.data(), all.size() * sizeof(int4), cudaMemcpyHostToDevice));
     a.ax.st = p->stages;
-    a.ay.st = p->stages + kMaxStages;
-    a.az.st = p->stages + 2 * kMaxStages;
+    a.ay.st = p->stages + 2 * kMaxStages;
+    a.az.st = p->stages + 4 * kMaxStages;
   }
   a.twx = p->tw;
   a.twy = p->tw + d.nx;
@@ -530,6 +612,7 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
 
   a.W = p->W;
   a.V = p->V;
+  a.err = p->err_dev;
   a.partials = p->partials;
   a.counter = p->counter;
   a.hist = p->hist;
@@ -544,12 +627,13 @@ void cbs_destroy(cbs_plan_t p) {
   cudaSetDevice(p->device);
   if (p->stream) cudaStreamSynchronize(p->stream);
   drop_graphs(p);
-  void* devs[] = {p->V, p->W, p->tw, p->stages, p->partials, p->counter, p->hist, p->adj_amp, p->dobj,
+  void* devs[] = {p->V, p->W, p->Ei, p->tw, p->stages, p->partials, p->counter, p->hist, p->adj_amp, p->dobj,
                   p->sx, p->sy, p->sz, p->pmin, p->pmax, p->pbad, p->pdev, p->eps_dev,
-                  p->Ef, p->Ea, p->grad_dev};
+                  p->Ef, p->Ea, p->grad_dev, p->err_dev};
   for (void* q : devs)
     if (q) cudaFree(q);
   if (p->hist_host) cudaFreeHost(p->hist_host);
+  if (p->err_host) cudaFreeHost(p->err_host);
   if (p->ev) cudaEventDestroy(p->ev);
   for (cudaEvent_t e : p->pev)
     if (e) cudaEventDestroy(e);
@@ -642,7 +726,8 @@ int cbs_set_permittivity(cbs_plan_t p, const float* eps) {
   for (int b = 0; b < B; ++b) epsilon = std::max(epsilon, dv[b]);
   if (!(epsilon > 0.0) || !std::isfinite(epsilon))
     return fail(CBS_ERR_ARG, "epsilon = %g: a lossless homogeneous grid has no convergent splitting", epsilon);
-  CK(launch_build_v(eps, p->d.nx, p->d.ny, p->d.nz, p->sx, p->sy, p->sz, kv2, k0sq, epsilon, p->V, p->stream));
+  CK(launch_build_v(eps, p->d.nx, p->d.ny, p->d.nz, p->base.nxp, p->sx, p->sy, p->sz, kv2, k0sq, epsilon, p->V,
+                    p->stream));
   CK(cudaStreamSynchronize(p->stream));
   p->k0sq_s = k0sq;
   p->eps_s = epsilon;

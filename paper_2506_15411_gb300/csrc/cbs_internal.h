@@ -1,24 +1,27 @@
 // cbs_internal.h -- structures shared by the host library and the CUDA kernels.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstddef>
 
 namespace cbs {
 
 constexpr int kMaxStages = 8;
+constexpr int kBoxRows = 64;   // at most this many rows (y or z) per tensor-copy box
 
 // Stockham radix plan of one axis: n = r[0] * r[1] * ... * r[ns-1]; a transform is run
 // by T = n / min(r) threads, each doing at most one radix-r butterfly per stage.  Per stage
 // q: Ns[q] = r[0] * ... * r[q-1], stride[q] = n / r[q] (butterflies, and the distance
 // between a butterfly's inputs), twstep[q] = n / (Ns[q] r[q]).
-// The per-stage table lives in device memory as int4 {r, Ns, stride, twstep} and is read
-// with uniform loads (a dynamically indexed kernel-parameter array would be copied to the
-// stack).
+// The per-stage table lives in device memory, two int4 per stage: {r, Ns, stride, twstep}
+// and {bits of 1/stride, bits of 1/Ns, 0, 0} (float reciprocals for exact small-integer
+// division); it is read with uniform loads (a dynamically indexed kernel-parameter array
+// would be copied to the stack).
 struct AxisPlan {
   int n;
   int ns;
   int T;
-  const int4* st;         // device table, ns entries
+  const int4* st;         // device table, 2 * ns entries
   int r[kMaxStages];      // host copy of the radices
 };
 
@@ -36,14 +39,18 @@ struct SourceArgs {
 // Everything one CBS iteration needs (kernel parameters, by value).
 struct IterArgs {
   int nx, ny, nz;
-  size_t N;
+  size_t N;               // nx * ny * nz (fields E, V, sources: dense rows)
+  int nxp;                // row pitch of the workspace W (multiple of 16 complex values)
+  size_t Nw;              // nxp * ny * nz: component stride of W
+  int yb, zb;             // rows per tensor-copy box along y and z
+  int nyr, nzr;           // ny, nz rounded up to whole boxes (shared-memory rows of a tile)
   AxisPlan ax, ay, az;
   const float2* twx;      // exp(-2 pi i m / n), m < n, per axis
   const float2* twy;
   const float2* twz;
-  float2* E;              // field [3][N]
-  float2* W;              // workspace [3][N]
-  const float2* V;        // potential [N], scaled
+  float2* E;              // field being iterated, [3][nz][ny][nxp] (plan-owned copy)
+  float2* W;              // workspace [3][nz][ny][nxp]
+  const float2* V;        // potential [nz][ny][nxp], scaled
   SourceArgs src;
   float inv_eps;          // 1 / epsilon (scaled)
   float2 kt2;             // k0^2 + i epsilon (scaled)
@@ -52,15 +59,16 @@ struct IterArgs {
   unsigned* counter;      // last-block-done counter (left at 0)
   double* hist;           // hist[slot] = sum |delta|^2 of this iteration
   int slot;
+  int* err;               // device error flag (a tensor-copy wait that timed out)
   // launch shapes
-  int rpb;                // rows per block, x passes
+  int rpb;                // rows per tile, x passes
   int tx_y, tx_z;         // x-columns per block, y and z passes
 };
 
 // Launchers (one per pass of an iteration); each returns the launch error.
 cudaError_t launch_xpass_fwd(const IterArgs& a, cudaStream_t s);   // W = FFTx(V E + S)
-cudaError_t launch_ypass(const IterArgs& a, bool inverse, cudaStream_t s);
-cudaError_t launch_zpass_green(const IterArgs& a, cudaStream_t s); // FFTz, G(p), IFFTz
+cudaError_t launch_ypass(const CUtensorMap& tm, const IterArgs& a, bool inverse, cudaStream_t s);
+cudaError_t launch_zpass_green(const CUtensorMap& tm, const IterArgs& a, cudaStream_t s);  // FFTz, G, IFFTz
 cudaError_t launch_xpass_inv_update(const IterArgs& a, cudaStream_t s);  // IFFTx, update, residual
 
 // Shared-memory bytes and threads of each pass for the plan's shapes.
@@ -75,7 +83,7 @@ cudaError_t launch_eps_minmax(const float* eps, size_t N, float* part_min, float
 cudaError_t launch_k2_maxdev(const float* eps, int nx, int ny, int nz, const double* sx,
                              const double* sy, const double* sz, double kv2, double k0sq,
                              double* part, int blocks, cudaStream_t s);
-cudaError_t launch_build_v(const float* eps, int nx, int ny, int nz, const double* sx,
+cudaError_t launch_build_v(const float* eps, int nx, int ny, int nz, int nxp, const double* sx,
                            const double* sy, const double* sz, double kv2, double k0sq,
                            double eps_shift, float2* V, cudaStream_t s);
 cudaError_t launch_adjoint_amp(const float2* E, size_t N, int nx, int ny, int x, int y, int z,

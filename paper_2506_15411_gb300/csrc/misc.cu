@@ -73,7 +73,8 @@ __global__ void k_k2_maxdev(const float* __restrict__ eps, int nx, int ny, int n
   if (threadIdx.x == 0) part[blockIdx.x] = m;
 }
 
-__global__ void k_build_v(const float* __restrict__ eps, int nx, int ny, int nz,
+// V in the padded row layout [nz][ny][nxp] of the iteration (the padding stays zero).
+__global__ void k_build_v(const float* __restrict__ eps, int nx, int ny, int nz, int nxp,
                           const double* __restrict__ sx, const double* __restrict__ sy,
                           const double* __restrict__ sz, double kv2, double k0sq, double eshift,
                           float2* __restrict__ V) {
@@ -83,7 +84,7 @@ __global__ void k_build_v(const float* __restrict__ eps, int nx, int ny, int nz,
     voxel_xyz(i, nx, ny, x, y, z);
     const double re = kv2 * (double)eps[i] - k0sq;
     const double im = kv2 * (sx[x] + sy[y] + sz[z]) - eshift;
-    V[i] = make_float2((float)re, (float)im);
+    V[((size_t)z * ny + y) * nxp + x] = make_float2((float)re, (float)im);
   }
 }
 
@@ -155,10 +156,10 @@ cudaError_t launch_k2_maxdev(const float* eps, int nx, int ny, int nz, const dou
   return cudaGetLastError();
 }
 
-cudaError_t launch_build_v(const float* eps, int nx, int ny, int nz, const double* sx,
+cudaError_t launch_build_v(const float* eps, int nx, int ny, int nz, int nxp, const double* sx,
                            const double* sy, const double* sz, double kv2, double k0sq,
                            double eshift, float2* V, cudaStream_t s) {
-  k_build_v<<<152 * 8, 256, 0, s>>>(eps, nx, ny, nz, sx, sy, sz, kv2, k0sq, eshift, V);
+  k_build_v<<<152 * 8, 256, 0, s>>>(eps, nx, ny, nz, nxp, sx, sy, sz, kv2, k0sq, eshift, V);
   return cudaGetLastError();
 }
 
