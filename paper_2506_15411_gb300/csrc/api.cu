@@ -18,6 +18,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <functional>
@@ -546,7 +547,6 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
     fail(CBS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the workspace");
     return bail(CBS_ERR_CUDA);
   }
-  CKP(cudaMalloc(&p->tw, (size_t)(d.nx + d.ny + d.nz) * sizeof(float2)));
   const int xb = xpass_blocks(a);
   CKP(cudaMalloc(&p->partials, (size_t)xb * sizeof(double)));
   CKP(cudaMalloc(&p->counter, sizeof(unsigned)));
@@ -564,16 +564,31 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
   CKP(cudaMalloc(&p->pbad, p->red_blocks * sizeof(int)));
   CKP(cudaMalloc(&p->pdev, p->red_blocks * sizeof(double)));
 
-  // twiddles exp(-2 pi i m / n) in FP64, rounded to FP32
-  std::vector<float2> tw;
+  // twiddles exp(-2 pi i m / n) in FP64, rounded to FP32; each axis' table starts on a
+  // 128-byte boundary and is copied whole into the tiles' shared memory (n * 8 bytes rounded
+  // up to a multiple of 16)
+  int twoff[3], twlen[3], twtot = 0;
+  for (int a2 = 0; a2 < 3; ++a2) {
+    twoff[a2] = twtot;
+    twlen[a2] = round_up(dims[a2] * (int)sizeof(float2), 16);
+    twtot += round_up(twlen[a2], 128);
+  }
+  std::vector<float2> tw(twtot / sizeof(float2), make_float2(0.f, 0.f));
   for (int a2 = 0; a2 < 3; ++a2) {
     const int n = dims[a2];
     for (int m = 0; m < n; ++m) {
       const double ang = -2.0 * kPiD * (double)m / (double)n;
-      tw.push_back(make_float2((float)std::cos(ang), (float)std::sin(ang)));
+      tw[twoff[a2] / sizeof(float2) + m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
     }
   }
-  CKP(cudaMemcpy(p->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  CKP(cudaMalloc(&p->tw, twtot));
+  CKP(cudaMemcpy(p->tw, tw.data(), twtot, cudaMemcpyHostToDevice));
+  a.twx = p->tw + twoff[0] / sizeof(float2);
+  a.twy = p->tw + twoff[1] / sizeof(float2);
+  a.twz = p->tw + twoff[2] / sizeof(float2);
+  a.twbx = twlen[0];
+  a.twby = twlen[1];
+  a.twbz = twlen[2];
   CKP(cudaMalloc(&p->stages, 3 * 2 * kMaxStages * sizeof(int4)));
   {
     std::vector<int4> all;
@@ -586,9 +601,19 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
     a.ay.st = p->stages + 2 * kMaxStages;
     a.az.st = p->stages + 4 * kMaxStages;
   }
-  a.twx = p->tw;
-  a.twy = p->tw + d.nx;
-  a.twz = p->tw + d.nx + d.ny;
+
+  // every address the tile kernels bulk-copy from or to must be 16-byte aligned, every size
+  // a multiple of 16 (checked here once: these pointers and sizes are fixed for the plan)
+  {
+    auto a16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
+    const bool ok = a16(a.twx) && a16(a.twy) && a16(a.twz) && a16(p->Ei) && a16(p->V) && a16(p->W) &&
+                    (a.twbx % 16 == 0) && (a.twby % 16 == 0) && (a.twbz % 16 == 0) &&
+                    ((size_t)a.nxp * sizeof(float2)) % 16 == 0 && (a.Nw * sizeof(float2)) % 16 == 0;
+    if (!ok) {
+      fail(CBS_ERR_CUDA, "internal: a bulk-copy address or size is not 16-byte aligned");
+      return bail(CBS_ERR_CUDA);
+    }
+  }
 
   // absorbing layers: sigma = sigma_max (t / L)^2 at depth t voxels into a layer of L voxels,
   // sigma_max = 3 n_bg ln(1e4) / (k_vac L pitch) (round-trip amplitude 1e-4), summed over axes

@@ -45,9 +45,10 @@ struct IterArgs {
   int yb, zb;             // rows per tensor-copy box along y and z
   int nyr, nzr;           // ny, nz rounded up to whole boxes (shared-memory rows of a tile)
   AxisPlan ax, ay, az;
-  const float2* twx;      // exp(-2 pi i m / n), m < n, per axis
+  const float2* twx;      // exp(-2 pi i m / n), m < n, per axis; each table 128-byte aligned
   const float2* twy;
   const float2* twz;
+  int twbx, twby, twbz;   // bytes copied per table: n * 8 rounded up to a multiple of 16
   float2* E;              // field being iterated, [3][nz][ny][nxp] (plan-owned copy)
   float2* W;              // workspace [3][nz][ny][nxp]
   const float2* V;        // potential [nz][ny][nxp], scaled

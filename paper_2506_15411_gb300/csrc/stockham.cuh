@@ -36,14 +36,15 @@ __device__ __forceinline__ float2 stage_inv(const AxisPlan& ap, int q) {
 // is at least 1/(2d) away from an integer, far more than the float rounding of the product.
 __device__ __forceinline__ int fdiv(int k, float inv) { return __float2int_rz(((float)k + 0.5f) * inv); }
 
+// tw: the axis' table w_n^m, m < n, in shared memory (copied in with the tile).
 template <int R, bool INV>
-__device__ __forceinline__ void twiddle_dft(float2* v, int kk, int twstep, const float2* __restrict__ tw) {
+__device__ __forceinline__ void twiddle_dft(float2* v, int kk, int twstep, const float2* tw) {
   if constexpr (R > 1) {
     if (kk > 0) {
       const int step = kk * twstep;
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        float2 w = __ldg(&tw[r * step]);
+        float2 w = tw[r * step];
         if (INV) w.y = -w.y;
         v[r] = cmul(v[r], w);
       }
@@ -55,7 +56,7 @@ __device__ __forceinline__ void twiddle_dft(float2* v, int kk, int twstep, const
 // ------------------------------------------------------------------- column tiles (y, z)
 template <int R, bool INV, int NCOL>
 __device__ __forceinline__ void stage_cols(const float2* src, float2* dst, int4 g, float invNs,
-                                           const float2* __restrict__ tw, int tid, int nth) {
+                                           const float2* tw, int tid, int nth) {
   const int stride = g.z, Ns = g.y;
   const int items = NCOL * stride;
   for (int k = tid; k < items; k += nth) {
@@ -75,7 +76,7 @@ __device__ __forceinline__ void stage_cols(const float2* src, float2* dst, int4 
 // FFT of the NCOL columns held in A, scratch B of the same layout; the result ends in A.
 // Every thread of the block must call it; it ends with a barrier.
 template <bool INV, int NCOL>
-__device__ __forceinline__ void fft_cols(float2* A, float2* B, const AxisPlan& ap, const float2* __restrict__ tw,
+__device__ __forceinline__ void fft_cols(float2* A, float2* B, const AxisPlan& ap, const float2* tw,
                                          int tid, int nth) {
   const int ns = ap.ns;
   float2* src = A;
@@ -96,9 +97,15 @@ __device__ __forceinline__ void fft_cols(float2* A, float2* B, const AxisPlan& a
 }
 
 // ------------------------------------------------------------------- row tiles (x)
+// Intermediate results of a row tile are stored swizzled: element A sits at
+// A ^ ((A >> 4) & 15), which keeps every group of 16 in place (rows start on multiples of 16)
+// and spreads the stride-R accesses of the early stages (Ns < 16) over all banks.
+__device__ __forceinline__ int swz(int a) { return a ^ ((a >> 4) & 15); }
+
 template <int R, bool INV>
-__device__ __forceinline__ void stage_rows(const float2* src, float2* dst, int nrows, int ncomp, int ld, int cs,
-                                           int4 g, float2 iv, const float2* __restrict__ tw, int tid, int nth) {
+__device__ __forceinline__ void stage_rows(const float2* src, float2* dst, bool sw_in, bool sw_out, int nrows,
+                                           int ncomp, int ld, int cs, int4 g, float2 iv,
+                                           const float2* tw, int tid, int nth) {
   const int stride = g.z, Ns = g.y;
   const int items = ncomp * nrows * stride;
   for (int k = tid; k < items; k += nth) {
@@ -108,37 +115,48 @@ __device__ __forceinline__ void stage_rows(const float2* src, float2* dst, int n
     const int base = c * cs + row * ld;
     float2 v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = src[base + j + r * stride];
+    for (int r = 0; r < R; ++r) {
+      const int a = base + j + r * stride;
+      v[r] = src[sw_in ? swz(a) : a];
+    }
     const int q = fdiv(j, iv.y);
     const int kk = j - q * Ns;
     twiddle_dft<R, INV>(v, kk, g.w, tw);
     const int d = q * Ns * R + kk;
 #pragma unroll
-    for (int r = 0; r < R; ++r) dst[base + d + r * Ns] = v[r];
+    for (int r = 0; r < R; ++r) {
+      const int a = base + d + r * Ns;
+      dst[sw_out ? swz(a) : a] = v[r];
+    }
   }
 }
 
-// FFT of nrows rows of ncomp components held in A (component stride cs, row stride ld),
-// scratch B of the same layout; the result ends in A.  Ends with a barrier.
+// FFT of nrows rows of ncomp components held in A (component stride cs, row stride ld; cs,
+// ld and the base of A multiples of 16), scratch B of the same layout.  Returns the buffer
+// holding the (unswizzled) result: A, or B when the last of several stages reads A (its
+// swizzled reads and unswizzled writes must not share a buffer).  Ends with a barrier.
 template <bool INV>
-__device__ __forceinline__ void fft_rows(float2* A, float2* B, int nrows, int ncomp, int ld, int cs,
-                                         const AxisPlan& ap, const float2* __restrict__ tw, int tid, int nth) {
+__device__ __forceinline__ float2* fft_rows(float2* A, float2* B, int nrows, int ncomp, int ld, int cs,
+                                            const AxisPlan& ap, const float2* tw, int tid, int nth) {
   const int ns = ap.ns;
   float2* src = A;
   float2* dst = B;
+  float2* out = A;
   for (int q = 0; q < ns; ++q) {
     const int4 g = stage_of(ap, q);
     const float2 iv = stage_inv(ap, q);
-    float2* out = (q == ns - 1) ? A : dst;
+    const bool last = (q == ns - 1);
+    out = !last ? dst : (q > 0 ? dst : A);
     radix_dispatch(g.x, [&](auto Ri) {
       constexpr int R = decltype(Ri)::value;
-      stage_rows<R, INV>(src, out, nrows, ncomp, ld, cs, g, iv, tw, tid, nth);
+      stage_rows<R, INV>(src, out, q > 0, !last, nrows, ncomp, ld, cs, g, iv, tw, tid, nth);
     });
     __syncthreads();
     float2* t = src;
     src = dst;
     dst = t;
   }
+  return out;
 }
 
 }  // namespace cbs

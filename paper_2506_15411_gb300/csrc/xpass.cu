@@ -75,13 +75,14 @@ struct XTile {
   float2* e;     // inverse: E tile
   float2* v;     // V tile
   float2* scr;   // scratch [3][rpb][nxp]
+  float2* tw;    // twiddle table of the x axis
   uint64_t* bar;
   int* fail;
   int* last;
   double* wsum;
 };
 
-__device__ __forceinline__ XTile carve(unsigned char* base, int rpb, int nxp, bool inverse) {
+__device__ __forceinline__ XTile carve(unsigned char* base, int rpb, int nxp, int twb, bool inverse) {
   const int span = rpb * nxp;
   float2* p = reinterpret_cast<float2*>(base);
   XTile t;
@@ -96,6 +97,8 @@ __device__ __forceinline__ XTile carve(unsigned char* base, int rpb, int nxp, bo
   p += span;
   t.scr = p;
   p += 3 * span;
+  t.tw = p;
+  p += twb / sizeof(float2);
   t.bar = reinterpret_cast<uint64_t*>(p);
   t.fail = reinterpret_cast<int*>(t.bar + 1);
   t.last = t.fail + 1;
@@ -109,13 +112,14 @@ __global__ void __launch_bounds__(kThreads) k_xpass_fwd(const IterArgs a) {
   const int r0 = blockIdx.x * rpb;
   const int nr = min(rpb, a.ny * a.nz - r0);
   const int span = rpb * nxp;
-  XTile t = carve(smem_raw, rpb, nxp, false);
+  XTile t = carve(smem_raw, rpb, nxp, a.twbx, false);
   if (!block_setup(t.in, t.bar, t.fail, a.err)) return;
   const uint32_t bytes = (uint32_t)(nr * nxp * sizeof(float2));
   if (threadIdx.x == 0) {
-    mbar_arrive_expect_tx(t.bar, 4 * bytes);
+    mbar_arrive_expect_tx(t.bar, 4 * bytes + a.twbx);
     for (int c = 0; c < 3; ++c) bulk_load(t.in + c * span, a.E + c * a.Nw + (size_t)r0 * nxp, bytes, t.bar);
     bulk_load(t.v, a.V + (size_t)r0 * nxp, bytes, t.bar);
+    bulk_load(t.tw, a.twx, a.twbx, t.bar);
   }
   if (!block_wait(t.bar, t.fail, a.err)) return;
   const int tid = threadIdx.x, nth = blockDim.x;
@@ -130,11 +134,11 @@ __global__ void __launch_bounds__(kThreads) k_xpass_fwd(const IterArgs a) {
     e = cadd(cmul(t.v[row * nxp + x], e), source_at(a, c, z, y, x));
   }
   __syncthreads();
-  fft_rows<false>(t.in, t.scr, nr, 3, nxp, span, a.ax, a.twx, tid, nth);
+  const float2* w = fft_rows<false>(t.in, t.scr, nr, 3, nxp, span, a.ax, t.tw, tid, nth);
   fence_async_smem();
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int c = 0; c < 3; ++c) bulk_store(a.W + c * a.Nw + (size_t)r0 * nxp, t.in + c * span, bytes);
+    for (int c = 0; c < 3; ++c) bulk_store(a.W + c * a.Nw + (size_t)r0 * nxp, w + c * span, bytes);
     bulk_commit();
     bulk_wait_all();
   }
@@ -146,11 +150,12 @@ __global__ void __launch_bounds__(kThreads) k_xpass_inv_update(const IterArgs a)
   const int r0 = blockIdx.x * rpb;
   const int nr = min(rpb, a.ny * a.nz - r0);
   const int span = rpb * nxp;
-  XTile t = carve(smem_raw, rpb, nxp, true);
+  XTile t = carve(smem_raw, rpb, nxp, a.twbx, true);
   if (!block_setup(t.in, t.bar, t.fail, a.err)) return;
   const uint32_t bytes = (uint32_t)(nr * nxp * sizeof(float2));
   if (threadIdx.x == 0) {
-    mbar_arrive_expect_tx(t.bar, 7 * bytes);
+    mbar_arrive_expect_tx(t.bar, 7 * bytes + a.twbx);
+    bulk_load(t.tw, a.twx, a.twbx, t.bar);
     for (int c = 0; c < 3; ++c) {
       bulk_load(t.in + c * span, a.W + c * a.Nw + (size_t)r0 * nxp, bytes, t.bar);
       bulk_load(t.e + c * span, a.E + c * a.Nw + (size_t)r0 * nxp, bytes, t.bar);
@@ -159,7 +164,7 @@ __global__ void __launch_bounds__(kThreads) k_xpass_inv_update(const IterArgs a)
   }
   if (!block_wait(t.bar, t.fail, a.err)) return;
   const int tid = threadIdx.x, nth = blockDim.x;
-  fft_rows<true>(t.in, t.scr, nr, 3, nxp, span, a.ax, a.twx, tid, nth);
+  const float2* w = fft_rows<true>(t.in, t.scr, nr, 3, nxp, span, a.ax, t.tw, tid, nth);
   const float ie = a.inv_eps;
   float acc = 0.f;
   for (int k = tid; k < nr * n; k += nth) {
@@ -170,7 +175,7 @@ __global__ void __launch_bounds__(kThreads) k_xpass_inv_update(const IterArgs a)
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const float2 e = t.e[c * span + o];
-      const float2 d = cmul(g, csub(e, t.in[c * span + o]));
+      const float2 d = cmul(g, csub(e, w[c * span + o]));
       t.e[c * span + o] = csub(e, d);
       acc = fmaf(d.x, d.x, fmaf(d.y, d.y, acc));
     }
@@ -187,9 +192,13 @@ __global__ void __launch_bounds__(kThreads) k_xpass_inv_update(const IterArgs a)
 
 }  // namespace
 
-// tiles, scratch, then 8 (mbarrier) + 8 (two flags) + 32 * 8 (warp sums) bytes
-size_t xpass_smem(const IterArgs& a) { return (size_t)10 * a.rpb * a.nxp * sizeof(float2) + 16 + 32 * 8; }
-size_t xpass_fwd_smem(const IterArgs& a) { return (size_t)7 * a.rpb * a.nxp * sizeof(float2) + 16 + 32 * 8; }
+// tiles, scratch, twiddles, then 8 (mbarrier) + 8 (two flags) + 32 * 8 (warp sums) bytes
+size_t xpass_smem(const IterArgs& a) {
+  return (size_t)10 * a.rpb * a.nxp * sizeof(float2) + a.twbx + 16 + 32 * 8;
+}
+size_t xpass_fwd_smem(const IterArgs& a) {
+  return (size_t)7 * a.rpb * a.nxp * sizeof(float2) + a.twbx + 16 + 32 * 8;
+}
 int xpass_blocks(const IterArgs& a) { return (a.ny * a.nz + a.rpb - 1) / a.rpb; }
 
 cudaError_t launch_xpass_fwd(const IterArgs& a, cudaStream_t s) {

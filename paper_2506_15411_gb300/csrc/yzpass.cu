@@ -47,17 +47,19 @@ __global__ void __launch_bounds__(256) k_ypass(const __grid_constant__ CUtensorM
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* tile = reinterpret_cast<float2*>(smem_raw);   // [nyr][TX]
   float2* scr = tile + a.nyr * TX;                       // [ny][TX]
-  uint64_t& bar = *reinterpret_cast<uint64_t*>(scr + a.ny * TX);
+  float2* tw = scr + a.ny * TX;                          // twiddles of the y axis
+  uint64_t& bar = *reinterpret_cast<uint64_t*>(tw + a.twby / sizeof(float2));
   int& fail = *reinterpret_cast<int*>(&bar + 1);
   const int x0 = blockIdx.x * TX, z = blockIdx.y, c = blockIdx.z;
   const int B = a.yb, nbox = a.nyr / B;
   if (!block_setup(tile, &bar, &fail, a.err)) return;
   if (threadIdx.x == 0) {
-    mbar_arrive_expect_tx(&bar, (uint32_t)(nbox * B * TX * sizeof(float2)));
+    mbar_arrive_expect_tx(&bar, (uint32_t)(nbox * B * TX * sizeof(float2)) + a.twby);
+    bulk_load(tw, a.twy, a.twby, &bar);
     for (int b = 0; b < nbox; ++b) tma_load_4d(tile + b * B * TX, &tm, x0, b * B, z, c, &bar);
   }
   if (!block_wait(&bar, &fail, a.err)) return;
-  fft_cols<INV, TX>(tile, scr, a.ay, a.twy, threadIdx.x, blockDim.x);
+  fft_cols<INV, TX>(tile, scr, a.ay, tw, threadIdx.x, blockDim.x);
   fence_async_smem();
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -73,19 +75,21 @@ __global__ void __launch_bounds__(256) k_zpass_green(const __grid_constant__ CUt
   const int nzr = a.nzr, n = a.nz;
   float2* tile = reinterpret_cast<float2*>(smem_raw);   // [3][nzr][TX]
   float2* scr = tile + 3 * nzr * TX;                     // [nz][TX]
-  uint64_t& bar = *reinterpret_cast<uint64_t*>(scr + n * TX);
+  float2* tw = scr + n * TX;                             // twiddles of the z axis
+  uint64_t& bar = *reinterpret_cast<uint64_t*>(tw + a.twbz / sizeof(float2));
   int& fail = *reinterpret_cast<int*>(&bar + 1);
   const int x0 = blockIdx.x * TX, y = blockIdx.y;
   const int B = a.zb, nbox = nzr / B;
   if (!block_setup(tile, &bar, &fail, a.err)) return;
   if (threadIdx.x == 0) {
-    mbar_arrive_expect_tx(&bar, (uint32_t)(3 * nbox * B * TX * sizeof(float2)));
+    mbar_arrive_expect_tx(&bar, (uint32_t)(3 * nbox * B * TX * sizeof(float2)) + a.twbz);
+    bulk_load(tw, a.twz, a.twbz, &bar);
     for (int c = 0; c < 3; ++c)
       for (int b = 0; b < nbox; ++b) tma_load_4d(tile + (c * nzr + b * B) * TX, &tm, x0, y, b * B, c, &bar);
   }
   if (!block_wait(&bar, &fail, a.err)) return;
   const int tid = threadIdx.x, nth = blockDim.x;
-  for (int c = 0; c < 3; ++c) fft_cols<false, TX>(tile + c * nzr * TX, scr, a.az, a.twz, tid, nth);
+  for (int c = 0; c < 3; ++c) fft_cols<false, TX>(tile + c * nzr * TX, scr, a.az, tw, tid, nth);
 
   const float two_pi = 6.283185307179586f;
   const float py = two_pi / (float)a.ny * (float)fft_freq(y, a.ny);
@@ -105,7 +109,7 @@ __global__ void __launch_bounds__(256) k_zpass_green(const __grid_constant__ CUt
     e[2 * nzr * TX] = X2;
   }
   __syncthreads();
-  for (int c = 0; c < 3; ++c) fft_cols<true, TX>(tile + c * nzr * TX, scr, a.az, a.twz, tid, nth);
+  for (int c = 0; c < 3; ++c) fft_cols<true, TX>(tile + c * nzr * TX, scr, a.az, tw, tid, nth);
   fence_async_smem();
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -129,9 +133,11 @@ cudaError_t with_tx(int tx, F&& f) {
 
 }  // namespace
 
-// tile + scratch + 16 bytes for the mbarrier and the failure flag
-size_t ypass_smem(const IterArgs& a) { return (size_t)(a.nyr + a.ny) * a.tx_y * sizeof(float2) + 16; }
-size_t zpass_smem(const IterArgs& a) { return (size_t)(3 * a.nzr + a.nz) * a.tx_z * sizeof(float2) + 16; }
+// tile + scratch + twiddles + 16 bytes for the mbarrier and the failure flag
+size_t ypass_smem(const IterArgs& a) { return (size_t)(a.nyr + a.ny) * a.tx_y * sizeof(float2) + a.twby + 16; }
+size_t zpass_smem(const IterArgs& a) {
+  return (size_t)(3 * a.nzr + a.nz) * a.tx_z * sizeof(float2) + a.twbz + 16;
+}
 
 cudaError_t launch_ypass(const CUtensorMap& tm, const IterArgs& a, bool inverse, cudaStream_t s) {
   dim3 grid((a.nx + a.tx_y - 1) / a.tx_y, a.nz, 3);
