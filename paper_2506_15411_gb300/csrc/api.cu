@@ -377,6 +377,7 @@ int run_series(cbs_plan_s* p, float2* E, const SourceArgs& src, bool warm, cbs_s
   const size_t rows = (size_t)3 * p->d.ny * p->d.nz;
   {
     cudaError_t e = cudaMemsetAsync(p->Ei, 0, 3 * a.Nw * sizeof(float2), p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->counter, 0, sizeof(unsigned), p->stream);
     if (e == cudaSuccess && warm)
       e = cudaMemcpy2DAsync(p->Ei, pad_row, E, dense_row, dense_row, rows, cudaMemcpyDeviceToDevice, p->stream);
     if (e != cudaSuccess) return S->status = fail(CBS_ERR_CUDA, "field copy-in: %s", cudaGetErrorString(e));
@@ -503,8 +504,8 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
     p->own_stream = true;         // the legacy stream cannot be captured
   }
   CKP(cudaEventCreateWithFlags(&p->ev, cudaEventDisableTiming));
-  CKP(xpass_set_smem_limit(200 * 1024));
-  CKP(yzpass_set_smem_limit(200 * 1024));
+  CKP(xpass_set_smem_limit(227 * 1024));
+  CKP(yzpass_set_smem_limit(227 * 1024));
 
   IterArgs& a = p->base;
   a.nx = d.nx;
@@ -514,21 +515,36 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
   a.ax = ax;
   a.ay = ay;
   a.az = az;
-  // launch shapes: ~256 threads per x-pass block; y and z tiles of TX columns by whole
-  // tensor-copy boxes, TX as wide as fits 2 blocks per SM (<= 113 KB of shared memory)
+  // launch shapes: persistent, double-buffered tile kernels, one block per SM (about 220 KB
+  // of shared memory each): x tiles of rpb rows, y and z tiles of TX columns by whole
+  // tensor-copy boxes, TX as wide as fits
+  const size_t kBlockBudget = 220 * 1024;
   a.nxp = round_up(d.nx, 16);
-  a.rpb = std::max(1, std::min(64, (int)((100 * 1024 - 272) / (80 * a.nxp))));   // x tile <= 100 KB
   a.Nw = (size_t)a.nxp * d.ny * d.nz;
+  {
+    const size_t per_row = (size_t)17 * a.nxp * sizeof(float2);   // the inverse x tile: 2 x 7 + 3 arrays
+    const size_t fixed = (size_t)round_up(d.nx * (int)sizeof(float2), 16) + 24 + 32 * 8;
+    a.rpb = (int)std::max<size_t>(1, std::min<size_t>(64, (kBlockBudget - fixed) / per_row));
+  }
   a.yb = std::min(kBoxRows, round_up(d.ny, 4));
   a.zb = std::min(kBoxRows, round_up(d.nz, 4));
   a.nyr = round_up(d.ny, a.yb);
   a.nzr = round_up(d.nz, a.zb);
-  const size_t kTileBudget = 113 * 1024;
-  a.tx_y = 16;
-  while (a.tx_y > 4 && (size_t)(a.nyr + d.ny) * a.tx_y * sizeof(float2) > kTileBudget) a.tx_y /= 2;
-  a.tx_z = 16;
-  while (a.tx_z > 4 && (size_t)(3 * a.nzr + d.nz) * a.tx_z * sizeof(float2) > kTileBudget) a.tx_z /= 2;
-  if (xpass_smem(a) > 200 * 1024 || ypass_smem(a) > 200 * 1024 || zpass_smem(a) > 200 * 1024) {
+  const size_t twy_b = round_up(d.ny * (int)sizeof(float2), 16), twz_b = round_up(d.nz * (int)sizeof(float2), 16);
+  auto ysmem = [&](int tx, int nb) { return (size_t)(nb * a.nyr + d.ny) * tx * sizeof(float2) + twy_b + 8 * nb + 8; };
+  auto zsmem = [&](int tx, int nb) { return (size_t)3 * (nb + 1) * a.nzr * tx * sizeof(float2) + twz_b + 8 * nb + 8; };
+  // widest tile with three buffers, else with two
+  bool fits = false;
+  for (int nb = 3; nb >= 2 && !fits; --nb)
+    for (int tx = 16; tx >= 8 && !fits; tx /= 2)
+      if (ysmem(tx, nb) <= kBlockBudget) { a.tx_y = tx; a.nbuf_y = nb; fits = true; }
+  if (!fits) { a.tx_y = 4; a.nbuf_y = 2; }
+  fits = false;
+  for (int nb = 3; nb >= 2 && !fits; --nb)
+    for (int tx = 16; tx >= 8 && !fits; tx /= 2)
+      if (zsmem(tx, nb) <= kBlockBudget) { a.tx_z = tx; a.nbuf_z = nb; fits = true; }
+  if (!fits) { a.tx_z = 4; a.nbuf_z = 2; }
+  if (ysmem(a.tx_y, a.nbuf_y) > kBlockBudget || zsmem(a.tx_z, a.nbuf_z) > kBlockBudget) {
     fail(CBS_ERR_ARG, "axis too long for the shared-memory tiles");
     return bail(CBS_ERR_ARG);
   }
@@ -547,8 +563,7 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
     fail(CBS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the workspace");
     return bail(CBS_ERR_CUDA);
   }
-  const int xb = xpass_blocks(a);
-  CKP(cudaMalloc(&p->partials, (size_t)xb * sizeof(double)));
+  CKP(cudaMalloc(&p->partials, (size_t)xpass_tiles(a) * sizeof(double)));   // >= the x grid
   CKP(cudaMalloc(&p->counter, sizeof(unsigned)));
   CKP(cudaMemset(p->counter, 0, sizeof(unsigned)));
   CKP(cudaMalloc(&p->hist, (size_t)d.check_every * sizeof(double)));
@@ -600,6 +615,14 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
     a.ax.st = p->stages;
     a.ay.st = p->stages + 2 * kMaxStages;
     a.az.st = p->stages + 4 * kMaxStages;
+  }
+
+  // persistent grid sizes (occupancy of each tile kernel at its shared-memory size)
+  {
+    int sms = 0;
+    CKP(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+    CKP(x_grid_size(a, sms));
+    CKP(yz_grid_sizes(a, sms));
   }
 
   // every address the tile kernels bulk-copy from or to must be 16-byte aligned, every size

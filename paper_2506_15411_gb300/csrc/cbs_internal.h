@@ -63,7 +63,9 @@ struct IterArgs {
   int* err;               // device error flag (a tensor-copy wait that timed out)
   // launch shapes
   int rpb;                // rows per tile, x passes
-  int tx_y, tx_z;         // x-columns per block, y and z passes
+  int tx_y, tx_z;         // x-columns per tile, y and z passes
+  int nbuf_y, nbuf_z;     // tile buffers of the pipelined y and z passes (2 or 3)
+  int grid_x, grid_xf, grid_y, grid_z;   // persistent grid sizes (x inverse, x forward, y, z)
 };
 
 // Launchers (one per pass of an iteration); each returns the launch error.
@@ -76,7 +78,9 @@ cudaError_t launch_xpass_inv_update(const IterArgs& a, cudaStream_t s);  // IFFT
 size_t xpass_smem(const IterArgs& a);
 size_t ypass_smem(const IterArgs& a);
 size_t zpass_smem(const IterArgs& a);
-int xpass_blocks(const IterArgs& a);
+int xpass_tiles(const IterArgs& a);
+cudaError_t yz_grid_sizes(IterArgs& a, int sms);   // sets grid_y, grid_z
+cudaError_t x_grid_size(IterArgs& a, int sms);     // sets grid_x, grid_xf
 
 // Set-up and gradient kernels (cbs_misc.cu).
 cudaError_t launch_eps_minmax(const float* eps, size_t N, float* part_min, float* part_max,

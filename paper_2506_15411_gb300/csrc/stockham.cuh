@@ -32,8 +32,9 @@ __device__ __forceinline__ float2 stage_inv(const AxisPlan& ap, int q) {
   return make_float2(__int_as_float(v.x), __int_as_float(v.y));
 }
 
-// floor(k / d) for 0 <= k < 2^20 and d <= 2^12 given inv = 1/d rounded to float: (k + 1/2)/d
-// is at least 1/(2d) away from an integer, far more than the float rounding of the product.
+// floor(k / d) for 0 <= k < 2^20 and 1 <= d <= 2^12 given inv = 1/d rounded to float:
+// (k + 1/2)/d is at least 1/(2d) away from an integer, far more than the float rounding of
+// the product.
 __device__ __forceinline__ int fdiv(int k, float inv) { return __float2int_rz(((float)k + 0.5f) * inv); }
 
 // tw: the axis' table w_n^m, m < n, in shared memory (copied in with the tile).
@@ -73,11 +74,17 @@ __device__ __forceinline__ void stage_cols(const float2* src, float2* dst, int4 
   }
 }
 
+struct NoHook {
+  __device__ __forceinline__ void operator()() const {}
+};
+
 // FFT of the NCOL columns held in A, scratch B of the same layout; the result ends in A.
+// `after_first` runs (in every thread) right after the first stage's barrier, when A is no
+// longer read by that stage: the pipelined kernels issue their next prefetch there.
 // Every thread of the block must call it; it ends with a barrier.
-template <bool INV, int NCOL>
+template <bool INV, int NCOL, class Hook = NoHook>
 __device__ __forceinline__ void fft_cols(float2* A, float2* B, const AxisPlan& ap, const float2* tw,
-                                         int tid, int nth) {
+                                         int tid, int nth, Hook after_first = Hook{}) {
   const int ns = ap.ns;
   float2* src = A;
   float2* dst = B;
@@ -90,10 +97,81 @@ __device__ __forceinline__ void fft_cols(float2* A, float2* B, const AxisPlan& a
       stage_cols<R, INV, NCOL>(src, out, g, iv.y, tw, tid, nth);
     });
     __syncthreads();
+    if (q == 0) after_first();
     float2* t = src;
     src = dst;
     dst = t;
   }
+}
+
+// ------------------------------------------------------------- column tiles, paired, multi-component
+// Element (c, i, col) at base[c * cs + i * NCOL + col].  An item transforms columns 2p and
+// 2p+1 of one component together: 16-byte shared-memory accesses, one twiddle load and one
+// set of index computations for both.  Items run p fastest, then j, then c.
+template <int R, bool INV, int NCOL>
+__device__ __forceinline__ void stage_cols2(const float2* src, float2* dst, int ncomp, int cs, int4 g, float2 iv,
+                                            const float2* tw, int tid, int nth) {
+  constexpr int NP = NCOL / 2;
+  const int stride = g.z, Ns = g.y;
+  const int items = ncomp * NP * stride;
+  for (int k = tid; k < items; k += nth) {
+    const int p = k % NP, rest = k / NP;
+    const int c = fdiv(rest, iv.x);
+    const int j = rest - c * stride;
+    const float4* s4 = reinterpret_cast<const float4*>(src + c * cs) + p;
+    float2 v0[R], v1[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float4 q = s4[(j + r * stride) * NP];
+      v0[r] = make_float2(q.x, q.y);
+      v1[r] = make_float2(q.z, q.w);
+    }
+    const int qq = fdiv(j, iv.y);
+    const int kk = j - qq * Ns;
+    if constexpr (R > 1) {
+      if (kk > 0) {
+        const int step = kk * g.w;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          float2 w = tw[r * step];
+          if (INV) w.y = -w.y;
+          v0[r] = cmul(v0[r], w);
+          v1[r] = cmul(v1[r], w);
+        }
+      }
+    }
+    DFT<R, INV>::run(v0);
+    DFT<R, INV>::run(v1);
+    const int d = qq * Ns * R + kk;
+    float4* d4 = reinterpret_cast<float4*>(dst + c * cs) + p;
+#pragma unroll
+    for (int r = 0; r < R; ++r) d4[(d + r * Ns) * NP] = make_float4(v0[r].x, v0[r].y, v1[r].x, v1[r].y);
+  }
+}
+
+// Stages [q0, q1) of the transform of ncomp x NCOL columns whose stage-q0 input is in `in`
+// (A or B; component stride cs), ping-ponging between A and B; a stage that is the last of
+// the transform writes A (its outputs sit where it read them, so that is safe from either
+// buffer).  Returns the buffer holding the output of stage q1 - 1.  Barrier after each stage;
+// `after_first` runs after the first of them.
+template <bool INV, int NCOL, class Hook = NoHook>
+__device__ __forceinline__ float2* cols2_stages(float2* in, float2* A, float2* B, int ncomp, int cs,
+                                                const AxisPlan& ap, int q0, int q1, const float2* tw, int tid,
+                                                int nth, Hook after_first = Hook{}) {
+  float2* src = in;
+  for (int q = q0; q < q1; ++q) {
+    const int4 g = stage_of(ap, q);
+    const float2 iv = stage_inv(ap, q);
+    float2* out = (q == ap.ns - 1) ? A : (src == A ? B : A);
+    radix_dispatch(g.x, [&](auto Ri) {
+      constexpr int R = decltype(Ri)::value;
+      stage_cols2<R, INV, NCOL>(src, out, ncomp, cs, g, iv, tw, tid, nth);
+    });
+    __syncthreads();
+    if (q == q0) after_first();
+    src = out;
+  }
+  return src;
 }
 
 // ------------------------------------------------------------------- row tiles (x)
@@ -108,10 +186,11 @@ __device__ __forceinline__ void stage_rows(const float2* src, float2* dst, bool 
                                            const float2* tw, int tid, int nth) {
   const int stride = g.z, Ns = g.y;
   const int items = ncomp * nrows * stride;
+  const float inv_rows = 1.0f / (float)nrows;
   for (int k = tid; k < items; k += nth) {
     const int t = fdiv(k, iv.x);           // (component, row) index
     const int j = k - t * stride;
-    const int c = t / nrows, row = t - c * nrows;
+    const int c = fdiv(t, inv_rows), row = t - c * nrows;
     const int base = c * cs + row * ld;
     float2 v[R];
 #pragma unroll
@@ -134,10 +213,12 @@ __device__ __forceinline__ void stage_rows(const float2* src, float2* dst, bool 
 // FFT of nrows rows of ncomp components held in A (component stride cs, row stride ld; cs,
 // ld and the base of A multiples of 16), scratch B of the same layout.  Returns the buffer
 // holding the (unswizzled) result: A, or B when the last of several stages reads A (its
-// swizzled reads and unswizzled writes must not share a buffer).  Ends with a barrier.
-template <bool INV>
+// swizzled reads and unswizzled writes must not share a buffer).  `after_first` as for
+// fft_cols.  Ends with a barrier.
+template <bool INV, class Hook = NoHook>
 __device__ __forceinline__ float2* fft_rows(float2* A, float2* B, int nrows, int ncomp, int ld, int cs,
-                                            const AxisPlan& ap, const float2* tw, int tid, int nth) {
+                                            const AxisPlan& ap, const float2* tw, int tid, int nth,
+                                            Hook after_first = Hook{}) {
   const int ns = ap.ns;
   float2* src = A;
   float2* dst = B;
@@ -152,6 +233,7 @@ __device__ __forceinline__ float2* fft_rows(float2* A, float2* B, int nrows, int
       stage_rows<R, INV>(src, out, q > 0, !last, nrows, ncomp, ld, cs, g, iv, tw, tid, nth);
     });
     __syncthreads();
+    if (q == 0) after_first();
     float2* t = src;
     src = dst;
     dst = t;

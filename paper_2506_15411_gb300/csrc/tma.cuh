@@ -93,6 +93,10 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 __device__ __forceinline__ void bulk_wait_read_all() {
   asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
+// All committed bulk groups but the newest one have finished reading their sources.
+__device__ __forceinline__ void bulk_wait_read_1() {
+  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
 
 // Order this thread's generic-proxy shared-memory writes before later async-proxy reads.
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -111,10 +115,22 @@ __device__ __forceinline__ bool block_setup(const void* tile, uint64_t* bar, int
   return *fail == 0;
 }
 
-// Bounded wait for the tile's copies, shared by the block: every thread polls; a timeout
-// anywhere aborts the whole block (uniformly) and records an error for the host.
-__device__ __forceinline__ bool block_wait(uint64_t* bar, int* fail, int* err) {
-  if (!mbar_wait(bar, 0)) *fail = 1;
+// Block set-up of a pipelined tile kernel: as block_setup, with `nbar` mbarriers.
+__device__ __forceinline__ bool block_setup_n(const void* tile, uint64_t* bars, int nbar, int* fail, int* err) {
+  if (threadIdx.x == 0) {
+    *fail = (smem_u32(tile) & 127u) ? 1 : 0;
+    if (*fail) atomicExch(err, kErrMisaligned);
+    for (int i = 0; i < nbar; ++i) mbar_init(bars + i, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  return *fail == 0;
+}
+
+// Bounded wait for phase `parity` of a tile's copies, shared by the block: every thread
+// polls; a timeout anywhere aborts the whole block (uniformly) and records an error.
+__device__ __forceinline__ bool block_wait(uint64_t* bar, int* fail, int* err, uint32_t parity = 0) {
+  if (!mbar_wait(bar, parity)) *fail = 1;
   __syncthreads();
   if (*fail) {
     if (threadIdx.x == 0) atomicExch(err, kErrTmaTimeout);

@@ -10,6 +10,8 @@
 // contiguous in the padded layouts of E, V and W (row pitch nxp, 16 complex values), so the
 // tile arrives with one bulk copy (cp.async.bulk) per array and component and leaves the same
 // way; the transforms run in shared memory with the ping-pong Stockham engine.
+#include <algorithm>
+
 #include "stockham.cuh"
 #include "tma.cuh"
 
@@ -66,17 +68,21 @@ __device__ __forceinline__ void residual_finish(float acc, const IterArgs& a, do
   }
 }
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 
-// Shared-memory layout of the x tiles: arrays of [3][rpb][nxp] (or [rpb][nxp] for V) complex,
-// then the mbarrier, the failure flag, the last-block flag and the warp sums.
+// Shared-memory layout of a pipelined x kernel: two buffer sets, each [3][rpb][nxp] of the
+// input (E forward, W inverse), [3][rpb][nxp] of E (inverse only), [rpb][nxp] of V and, in
+// the forward kernel, its own scratch [3][rpb][nxp] (an odd number of FFT stages leaves the
+// result there, to be stored while the other set computes); then the inverse kernel's shared
+// scratch, the x twiddles, two mbarriers, flags and warp sums.
 struct XTile {
-  float2* in;    // forward: E tile;  inverse: W tile
-  float2* e;     // inverse: E tile
-  float2* v;     // V tile
-  float2* scr;   // scratch [3][rpb][nxp]
-  float2* tw;    // twiddle table of the x axis
-  uint64_t* bar;
+  float2* in0;      // buffer set 0; set 1 starts `set` elements later
+  float2* e0;
+  float2* v0;
+  int set;
+  float2* scr;
+  float2* tw;
+  uint64_t* full;   // [2]
   int* fail;
   int* last;
   double* wsum;
@@ -86,128 +92,190 @@ __device__ __forceinline__ XTile carve(unsigned char* base, int rpb, int nxp, in
   const int span = rpb * nxp;
   float2* p = reinterpret_cast<float2*>(base);
   XTile t;
-  t.in = p;
-  p += 3 * span;
-  t.e = nullptr;
+  t.set = 7 * span;
+  t.in0 = p;
+  t.e0 = inverse ? p + 3 * span : nullptr;
+  t.v0 = p + (inverse ? 6 : 3) * span;
+  p += 2 * t.set;
   if (inverse) {
-    t.e = p;
+    t.scr = p;            // shared by both sets
     p += 3 * span;
+  } else {
+    t.scr = t.v0 + span;  // set 0's scratch; set k's is t.scr + k * t.set
   }
-  t.v = p;
-  p += span;
-  t.scr = p;
-  p += 3 * span;
   t.tw = p;
   p += twb / sizeof(float2);
-  t.bar = reinterpret_cast<uint64_t*>(p);
-  t.fail = reinterpret_cast<int*>(t.bar + 1);
+  t.full = reinterpret_cast<uint64_t*>(p);
+  t.fail = reinterpret_cast<int*>(t.full + 2);
   t.last = t.fail + 1;
-  t.wsum = reinterpret_cast<double*>(t.bar + 2);
+  t.wsum = reinterpret_cast<double*>(t.full + 3);
   return t;
 }
 
-__global__ void __launch_bounds__(kThreads) k_xpass_fwd(const IterArgs a) {
+__device__ __forceinline__ int x_tiles(const IterArgs& a) { return (a.ny * a.nz + a.rpb - 1) / a.rpb; }
+
+// Persistent, double-buffered forward x pass: tile i is transformed in one buffer set while
+// the bulk copies of tile i+1 land in the other (issued after the first FFT stage, once the
+// store of tile i-1 from that set has left shared memory), and the store of tile i drains
+// during the next tile.
+__global__ void __launch_bounds__(kThreads, 1) k_xpass_fwd(const IterArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int rpb = a.rpb, nxp = a.nxp, n = a.nx;
-  const int r0 = blockIdx.x * rpb;
-  const int nr = min(rpb, a.ny * a.nz - r0);
   const int span = rpb * nxp;
+  const int rows = a.ny * a.nz, ntiles = x_tiles(a);
   XTile t = carve(smem_raw, rpb, nxp, a.twbx, false);
-  if (!block_setup(t.in, t.bar, t.fail, a.err)) return;
-  const uint32_t bytes = (uint32_t)(nr * nxp * sizeof(float2));
-  if (threadIdx.x == 0) {
-    mbar_arrive_expect_tx(t.bar, 4 * bytes + a.twbx);
-    for (int c = 0; c < 3; ++c) bulk_load(t.in + c * span, a.E + c * a.Nw + (size_t)r0 * nxp, bytes, t.bar);
-    bulk_load(t.v, a.V + (size_t)r0 * nxp, bytes, t.bar);
-    bulk_load(t.tw, a.twx, a.twbx, t.bar);
-  }
-  if (!block_wait(t.bar, t.fail, a.err)) return;
+  int tile = blockIdx.x;
+  if (tile >= ntiles) return;
+  if (!block_setup_n(t.in0, t.full, 2, t.fail, a.err)) return;
   const int tid = threadIdx.x, nth = blockDim.x;
-  // V E + S in place (the row padding stays as loaded: zeros)
-  for (int k = tid; k < 3 * nr * n; k += nth) {
-    const int c = k / (nr * n);
-    const int rem = k - c * nr * n;
-    const int row = rem / n, x = rem - row * n;
-    const int gr = r0 + row;
-    const int z = gr / a.ny, y = gr - z * a.ny;
-    float2& e = t.in[c * span + row * nxp + x];
-    e = cadd(cmul(t.v[row * nxp + x], e), source_at(a, c, z, y, x));
+  const float inv_n = 1.0f / (float)n, inv_ny = 1.0f / (float)a.ny;
+  auto issue = [&](int tt, int k, uint32_t extra) {
+    const int r0 = tt * rpb, nr = min(rpb, rows - r0);
+    const uint32_t bytes = (uint32_t)(nr * nxp * sizeof(float2));
+    mbar_arrive_expect_tx(&t.full[k], 4 * bytes + extra);
+    for (int c = 0; c < 3; ++c) bulk_load(t.in0 + k * t.set + c * span, a.E + c * a.Nw + (size_t)r0 * nxp, bytes, &t.full[k]);
+    bulk_load(t.v0 + k * t.set, a.V + (size_t)r0 * nxp, bytes, &t.full[k]);
+  };
+  if (tid == 0) {
+    issue(tile, 0, a.twbx);
+    bulk_load(t.tw, a.twx, a.twbx, &t.full[0]);
   }
-  __syncthreads();
-  const float2* w = fft_rows<false>(t.in, t.scr, nr, 3, nxp, span, a.ax, t.tw, tid, nth);
-  fence_async_smem();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int c = 0; c < 3; ++c) bulk_store(a.W + c * a.Nw + (size_t)r0 * nxp, w + c * span, bytes);
-    bulk_commit();
-    bulk_wait_all();
+  for (int i = 0; tile < ntiles; ++i, tile += gridDim.x) {
+    const int k = i & 1;
+    const int r0 = tile * rpb, nr = min(rpb, rows - r0);
+    const int tn = tile + gridDim.x;
+    if (!block_wait(&t.full[k], t.fail, a.err, (uint32_t)((i >> 1) & 1))) return;
+    float2* in = t.in0 + k * t.set;
+    const float2* v = t.v0 + k * t.set;
+    // V E + S in place (the row padding stays as loaded)
+    for (int q = tid; q < nr * n; q += nth) {
+      const int row = fdiv(q, inv_n), x = q - row * n;
+      const int gr = r0 + row;
+      const int z = fdiv(gr, inv_ny), y = gr - z * a.ny;
+      const int o = row * nxp + x;
+      const float2 vv = v[o];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) in[c * span + o] = cadd(cmul(vv, in[c * span + o]), source_at(a, c, z, y, x));
+    }
+    __syncthreads();
+    auto prefetch = [&] {
+      if (tid == 0 && tn < ntiles) {
+        bulk_wait_read_all();   // the store of tile i-1 (from set k^1) has left shared memory
+        issue(tn, k ^ 1, 0);
+      }
+    };
+    const float2* w = fft_rows<false>(in, t.scr + k * t.set, nr, 3, nxp, span, a.ax, t.tw, tid, nth, prefetch);
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      const uint32_t bytes = (uint32_t)(nr * nxp * sizeof(float2));
+      for (int c = 0; c < 3; ++c) bulk_store(a.W + c * a.Nw + (size_t)r0 * nxp, w + c * span, bytes);
+      bulk_commit();
+    }
   }
+  if (tid == 0) bulk_wait_all();
 }
 
-__global__ void __launch_bounds__(kThreads) k_xpass_inv_update(const IterArgs a) {
+// Persistent, double-buffered inverse x pass with the update and the FP64 residual.
+__global__ void __launch_bounds__(kThreads, 1) k_xpass_inv_update(const IterArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int rpb = a.rpb, nxp = a.nxp, n = a.nx;
-  const int r0 = blockIdx.x * rpb;
-  const int nr = min(rpb, a.ny * a.nz - r0);
   const int span = rpb * nxp;
+  const int rows = a.ny * a.nz, ntiles = x_tiles(a);
   XTile t = carve(smem_raw, rpb, nxp, a.twbx, true);
-  if (!block_setup(t.in, t.bar, t.fail, a.err)) return;
-  const uint32_t bytes = (uint32_t)(nr * nxp * sizeof(float2));
-  if (threadIdx.x == 0) {
-    mbar_arrive_expect_tx(t.bar, 7 * bytes + a.twbx);
-    bulk_load(t.tw, a.twx, a.twbx, t.bar);
-    for (int c = 0; c < 3; ++c) {
-      bulk_load(t.in + c * span, a.W + c * a.Nw + (size_t)r0 * nxp, bytes, t.bar);
-      bulk_load(t.e + c * span, a.E + c * a.Nw + (size_t)r0 * nxp, bytes, t.bar);
-    }
-    bulk_load(t.v, a.V + (size_t)r0 * nxp, bytes, t.bar);
-  }
-  if (!block_wait(t.bar, t.fail, a.err)) return;
-  const int tid = threadIdx.x, nth = blockDim.x;
-  const float2* w = fft_rows<true>(t.in, t.scr, nr, 3, nxp, span, a.ax, t.tw, tid, nth);
-  const float ie = a.inv_eps;
+  int tile = blockIdx.x;
   float acc = 0.f;
-  for (int k = tid; k < nr * n; k += nth) {
-    const int row = k / n, x = k - row * n;
-    const int o = row * nxp + x;
-    const float2 v = t.v[o];
-    const float2 g = make_float2(-v.y * ie, v.x * ie);   // gamma = (i / epsilon) V
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const float2 e = t.e[c * span + o];
-      const float2 d = cmul(g, csub(e, w[c * span + o]));
-      t.e[c * span + o] = csub(e, d);
-      acc = fmaf(d.x, d.x, fmaf(d.y, d.y, acc));
+  const int tid = threadIdx.x, nth = blockDim.x;
+  if (tile < ntiles) {
+    if (!block_setup_n(t.in0, t.full, 2, t.fail, a.err)) return;
+    auto issue = [&](int tt, int k, uint32_t extra) {
+      const int r0 = tt * rpb, nr = min(rpb, rows - r0);
+      const uint32_t bytes = (uint32_t)(nr * nxp * sizeof(float2));
+      mbar_arrive_expect_tx(&t.full[k], 7 * bytes + extra);
+      for (int c = 0; c < 3; ++c) {
+        bulk_load(t.in0 + k * t.set + c * span, a.W + c * a.Nw + (size_t)r0 * nxp, bytes, &t.full[k]);
+        bulk_load(t.e0 + k * t.set + c * span, a.E + c * a.Nw + (size_t)r0 * nxp, bytes, &t.full[k]);
+      }
+      bulk_load(t.v0 + k * t.set, a.V + (size_t)r0 * nxp, bytes, &t.full[k]);
+    };
+    if (tid == 0) {
+      issue(tile, 0, a.twbx);
+      bulk_load(t.tw, a.twx, a.twbx, &t.full[0]);
     }
-  }
-  fence_async_smem();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int c = 0; c < 3; ++c) bulk_store(a.E + c * a.Nw + (size_t)r0 * nxp, t.e + c * span, bytes);
-    bulk_commit();
+    const float ie = a.inv_eps;
+    const float inv_n = 1.0f / (float)n;
+    for (int i = 0; tile < ntiles; ++i, tile += gridDim.x) {
+      const int k = i & 1;
+      const int r0 = tile * rpb, nr = min(rpb, rows - r0);
+      const int tn = tile + gridDim.x;
+      if (!block_wait(&t.full[k], t.fail, a.err, (uint32_t)((i >> 1) & 1))) return;
+      auto prefetch = [&] {
+        if (tid == 0 && tn < ntiles) {
+          bulk_wait_read_all();   // the store of tile i-1 (from set k^1) has left shared memory
+          issue(tn, k ^ 1, 0);
+        }
+      };
+      const float2* w = fft_rows<true>(t.in0 + k * t.set, t.scr, nr, 3, nxp, span, a.ax, t.tw, tid, nth, prefetch);
+      float2* e = t.e0 + k * t.set;
+      const float2* v = t.v0 + k * t.set;
+      for (int q = tid; q < nr * n; q += nth) {
+        const int row = fdiv(q, inv_n), x = q - row * n;
+        const int o = row * nxp + x;
+        const float2 vv = v[o];
+        const float2 g = make_float2(-vv.y * ie, vv.x * ie);   // gamma = (i / epsilon) V
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float2 ec = e[c * span + o];
+          const float2 d = cmul(g, csub(ec, w[c * span + o]));
+          e[c * span + o] = csub(ec, d);
+          acc = fmaf(d.x, d.x, fmaf(d.y, d.y, acc));
+        }
+      }
+      fence_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        const uint32_t bytes = (uint32_t)(nr * nxp * sizeof(float2));
+        for (int c = 0; c < 3; ++c) bulk_store(a.E + c * a.Nw + (size_t)r0 * nxp, e + c * span, bytes);
+        bulk_commit();
+      }
+    }
   }
   residual_finish(acc, a, t.wsum, t.last);
-  if (threadIdx.x == 0) bulk_wait_all();
+  if (tid == 0) bulk_wait_all();
 }
 
 }  // namespace
 
-// tiles, scratch, twiddles, then 8 (mbarrier) + 8 (two flags) + 32 * 8 (warp sums) bytes
+// two buffer sets, scratch, twiddles, then 16 (two mbarriers) + 8 (two flags) + 32 * 8
+// (warp sums) bytes
 size_t xpass_smem(const IterArgs& a) {
-  return (size_t)10 * a.rpb * a.nxp * sizeof(float2) + a.twbx + 16 + 32 * 8;
+  return (size_t)17 * a.rpb * a.nxp * sizeof(float2) + a.twbx + 24 + 32 * 8;
 }
 size_t xpass_fwd_smem(const IterArgs& a) {
-  return (size_t)7 * a.rpb * a.nxp * sizeof(float2) + a.twbx + 16 + 32 * 8;
+  return (size_t)14 * a.rpb * a.nxp * sizeof(float2) + a.twbx + 24 + 32 * 8;
 }
-int xpass_blocks(const IterArgs& a) { return (a.ny * a.nz + a.rpb - 1) / a.rpb; }
+int xpass_tiles(const IterArgs& a) { return (a.ny * a.nz + a.rpb - 1) / a.rpb; }
+
+// Persistent grids: as many blocks as fit at once (the inverse pass's, which is also the
+// number of residual partials), capped by the tile count.
+cudaError_t x_grid_size(IterArgs& a, int sms) {
+  int occ_f = 0, occ_i = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, k_xpass_fwd, kThreads, xpass_fwd_smem(a));
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_i, k_xpass_inv_update, kThreads, xpass_smem(a));
+  if (e != cudaSuccess) return e;
+  a.grid_x = std::max(1, std::min(xpass_tiles(a), sms * std::max(1, occ_i)));
+  a.grid_xf = std::max(1, std::min(xpass_tiles(a), sms * std::max(1, occ_f)));
+  return cudaSuccess;
+}
 
 cudaError_t launch_xpass_fwd(const IterArgs& a, cudaStream_t s) {
-  k_xpass_fwd<<<xpass_blocks(a), kThreads, xpass_fwd_smem(a), s>>>(a);
+  k_xpass_fwd<<<a.grid_xf, kThreads, xpass_fwd_smem(a), s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_xpass_inv_update(const IterArgs& a, cudaStream_t s) {
-  k_xpass_inv_update<<<xpass_blocks(a), kThreads, xpass_smem(a), s>>>(a);
+  k_xpass_inv_update<<<a.grid_x, kThreads, xpass_smem(a), s>>>(a);
   return cudaGetLastError();
 }
 

@@ -11,6 +11,8 @@
 // shared memory with the ping-pong Stockham engine, and writes it back with tensor stores.
 // The workspace W has a padded row pitch (nxp, a multiple of 16 complex values) so that every
 // tensor stride is a multiple of 16 bytes and every box row starts on a 128-byte boundary.
+#include <algorithm>
+
 #include "stockham.cuh"
 #include "tma.cuh"
 
@@ -42,83 +44,186 @@ __device__ __forceinline__ void green(float px, float py, float pz, float qx, fl
   X2 = cmul(make_float2(X2.x + qz * c.x, X2.y + qz * c.y), inv);
 }
 
+constexpr int kYZThreads = 512;
+
+// Persistent, multi-buffered y pass: a block walks tiles t = blockIdx.x, + gridDim.x, ...
+// through nbuf tile buffers (3 when they fit, else 2); while it transforms tile i, the tensor
+// copies of tile i+1 land in the next buffer (issued after the first FFT stage, once the store
+// of the tile that last used that buffer has been read out; with 3 buffers that store was
+// issued a whole tile earlier), and the store of tile i drains meanwhile.  Twiddles are
+// loaded once.
 template <int TX, bool INV>
-__global__ void __launch_bounds__(256) k_ypass(const __grid_constant__ CUtensorMap tm, const IterArgs a) {
+__global__ void __launch_bounds__(kYZThreads, 1) k_ypass(const __grid_constant__ CUtensorMap tm, const IterArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  float2* tile = reinterpret_cast<float2*>(smem_raw);   // [nyr][TX]
-  float2* scr = tile + a.nyr * TX;                       // [ny][TX]
+  const int tileN = a.nyr * TX, nbuf = a.nbuf_y;
+  float2* buf0 = reinterpret_cast<float2*>(smem_raw);   // nbuf x [nyr][TX]
+  float2* scr = buf0 + nbuf * tileN;                     // [ny][TX]
   float2* tw = scr + a.ny * TX;                          // twiddles of the y axis
-  uint64_t& bar = *reinterpret_cast<uint64_t*>(tw + a.twby / sizeof(float2));
-  int& fail = *reinterpret_cast<int*>(&bar + 1);
-  const int x0 = blockIdx.x * TX, z = blockIdx.y, c = blockIdx.z;
+  uint64_t* full = reinterpret_cast<uint64_t*>(tw + a.twby / sizeof(float2));   // [nbuf]
+  int* fail = reinterpret_cast<int*>(full + nbuf);
+  const int nxt = (a.nx + TX - 1) / TX;
+  const int ntiles = nxt * a.nz * 3;
   const int B = a.yb, nbox = a.nyr / B;
-  if (!block_setup(tile, &bar, &fail, a.err)) return;
-  if (threadIdx.x == 0) {
-    mbar_arrive_expect_tx(&bar, (uint32_t)(nbox * B * TX * sizeof(float2)) + a.twby);
-    bulk_load(tw, a.twy, a.twby, &bar);
-    for (int b = 0; b < nbox; ++b) tma_load_4d(tile + b * B * TX, &tm, x0, b * B, z, c, &bar);
+  const uint32_t tile_bytes = (uint32_t)(nbox * B * TX * sizeof(float2));
+  int t = blockIdx.x;
+  if (t >= ntiles) return;
+  if (!block_setup_n(buf0, full, nbuf, fail, a.err)) return;
+  auto issue = [&](int tt, float2* buf, uint64_t* bar) {
+    const int xt = tt % nxt, r = tt / nxt;
+    const int z = r % a.nz, c = r / a.nz;
+    for (int b = 0; b < nbox; ++b) tma_load_4d(buf + b * B * TX, &tm, xt * TX, b * B, z, c, bar);
+  };
+  const int tid = threadIdx.x, nth = blockDim.x;
+  if (tid == 0) {
+    mbar_arrive_expect_tx(&full[0], tile_bytes + a.twby);
+    bulk_load(tw, a.twy, a.twby, &full[0]);
+    issue(t, buf0, &full[0]);
   }
-  if (!block_wait(&bar, &fail, a.err)) return;
-  fft_cols<INV, TX>(tile, scr, a.ay, tw, threadIdx.x, blockDim.x);
-  fence_async_smem();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int b = 0; b < nbox; ++b) tma_store_4d(&tm, x0, b * B, z, c, tile + b * B * TX);
-    bulk_commit();
-    bulk_wait_all();
+  for (int i = 0, b = 0; t < ntiles; ++i, t += gridDim.x, b = (b + 1 == nbuf) ? 0 : b + 1) {
+    float2* cur = buf0 + b * tileN;
+    const int bn = (b + 1 == nbuf) ? 0 : b + 1;
+    float2* nxb = buf0 + bn * tileN;
+    uint64_t* nbar = &full[bn];
+    const int tn = t + gridDim.x;
+    if (!block_wait(&full[b], fail, a.err, (uint32_t)((i / nbuf) & 1))) return;
+    auto prefetch = [&] {
+      if (tid == 0 && tn < ntiles) {
+        if (nbuf == 2) bulk_wait_read_all();   // the store of tile i-1 has left nxb
+        else bulk_wait_read_1();               // all but the newest store (tile i-1) have
+        mbar_arrive_expect_tx(nbar, tile_bytes);
+        issue(tn, nxb, nbar);
+      }
+    };
+    cols2_stages<INV, TX>(cur, cur, scr, 1, 0, a.ay, 0, a.ay.ns, tw, tid, nth, prefetch);
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      const int xt = t % nxt, r = t / nxt;
+      const int z = r % a.nz, c = r / a.nz;
+      for (int b = 0; b < nbox; ++b) tma_store_4d(&tm, xt * TX, b * B, z, c, cur + b * B * TX);
+      bulk_commit();
+    }
   }
+  if (tid == 0) bulk_wait_all();
 }
 
-template <int TX>
-__global__ void __launch_bounds__(256) k_zpass_green(const __grid_constant__ CUtensorMap tm, const IterArgs a) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int nzr = a.nzr, n = a.nz;
-  float2* tile = reinterpret_cast<float2*>(smem_raw);   // [3][nzr][TX]
-  float2* scr = tile + 3 * nzr * TX;                     // [nz][TX]
-  float2* tw = scr + n * TX;                             // twiddles of the z axis
-  uint64_t& bar = *reinterpret_cast<uint64_t*>(tw + a.twbz / sizeof(float2));
-  int& fail = *reinterpret_cast<int*>(&bar + 1);
-  const int x0 = blockIdx.x * TX, y = blockIdx.y;
-  const int B = a.zb, nbox = nzr / B;
-  if (!block_setup(tile, &bar, &fail, a.err)) return;
-  if (threadIdx.x == 0) {
-    mbar_arrive_expect_tx(&bar, (uint32_t)(3 * nbox * B * TX * sizeof(float2)) + a.twbz);
-    bulk_load(tw, a.twz, a.twbz, &bar);
-    for (int c = 0; c < 3; ++c)
-      for (int b = 0; b < nbox; ++b) tma_load_4d(tile + (c * nzr + b * B) * TX, &tm, x0, y, b * B, c, &bar);
-  }
-  if (!block_wait(&bar, &fail, a.err)) return;
-  const int tid = threadIdx.x, nth = blockDim.x;
-  for (int c = 0; c < 3; ++c) fft_cols<false, TX>(tile + c * nzr * TX, scr, a.az, tw, tid, nth);
-
+// Last forward z stage of the three components of one column (outputs in natural order,
+// at the positions it reads), the k-space multiply at its R outputs, written to A.
+template <int R, int TX>
+__device__ __forceinline__ void stage_last_green(const float2* src, float2* A, int cs, int4 g, const float2* tw,
+                                                 int tid, int nth, int x0, float py, float qy, const IterArgs& a) {
+  const int stride = g.z, n = a.nz;
+  const int items = TX * stride;
   const float two_pi = 6.283185307179586f;
-  const float py = two_pi / (float)a.ny * (float)fft_freq(y, a.ny);
-  const float qy = (2 * y == a.ny) ? 0.f : py;
-  for (int k = tid; k < n * TX; k += nth) {
-    const int col = k % TX, i = k / TX;
+  for (int k = tid; k < items; k += nth) {
+    const int col = k % TX, j = k / TX;
+    float2 v[3][R];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[c][r] = src[c * cs + (j + r * stride) * TX + col];
+    // last stage: Ns = n / R = stride, so j mod Ns = j
+    if constexpr (R > 1) {
+      if (j > 0) {
+        const int step = j * g.w;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          const float2 w = tw[r * step];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) v[c][r] = cmul(v[c][r], w);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) DFT<R, false>::run(v[c]);
     const int x = x0 + col;
     const float px = two_pi / (float)a.nx * (float)fft_freq(x, a.nx);
     const float qx = (2 * x == a.nx) ? 0.f : px;
-    const float pz = two_pi / (float)n * (float)fft_freq(i, n);
-    const float qz = (2 * i == n) ? 0.f : pz;
-    float2* e = tile + i * TX + col;
-    float2 X0 = e[0], X1 = e[nzr * TX], X2 = e[2 * nzr * TX];
-    green(px, py, pz, qx, qy, qz, a.kt2, a.invN, X0, X1, X2);
-    e[0] = X0;
-    e[nzr * TX] = X1;
-    e[2 * nzr * TX] = X2;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int iz = j + r * stride;
+      const float pz = two_pi / (float)n * (float)fft_freq(iz, n);
+      const float qz = (2 * iz == n) ? 0.f : pz;
+      green(px, py, pz, qx, qy, qz, a.kt2, a.invN, v[0][r], v[1][r], v[2][r]);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) A[c * cs + iz * TX + col] = v[c][r];
+    }
   }
-  __syncthreads();
-  for (int c = 0; c < 3; ++c) fft_cols<true, TX>(tile + c * nzr * TX, scr, a.az, tw, tid, nth);
-  fence_async_smem();
-  __syncthreads();
-  if (threadIdx.x == 0) {
+}
+
+// Persistent, multi-buffered z pass (same pipeline as the y pass): FFT_z of the three
+// components of a tile (their stages run together), the k-space multiply fused into the last
+// forward stage, IFFT_z.
+template <int TX>
+__global__ void __launch_bounds__(kYZThreads, 1) k_zpass_green(const __grid_constant__ CUtensorMap tm,
+                                                               const IterArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int nzr = a.nzr;
+  const int cs = nzr * TX, tileN = 3 * cs, nbuf = a.nbuf_z;
+  float2* buf0 = reinterpret_cast<float2*>(smem_raw);   // nbuf x [3][nzr][TX]
+  float2* scr = buf0 + nbuf * tileN;                     // [3][nzr][TX]
+  float2* tw = scr + tileN;                              // twiddles of the z axis
+  uint64_t* full = reinterpret_cast<uint64_t*>(tw + a.twbz / sizeof(float2));   // [nbuf]
+  int* fail = reinterpret_cast<int*>(full + nbuf);
+  const int nxt = (a.nx + TX - 1) / TX;
+  const int ntiles = nxt * a.ny;
+  const int B = a.zb, nbox = nzr / B;
+  const uint32_t tile_bytes = (uint32_t)(3 * nbox * B * TX * sizeof(float2));
+  int t = blockIdx.x;
+  if (t >= ntiles) return;
+  if (!block_setup_n(buf0, full, nbuf, fail, a.err)) return;
+  auto issue = [&](int tt, float2* buf, uint64_t* bar) {
+    const int xt = tt % nxt, y = tt / nxt;
     for (int c = 0; c < 3; ++c)
-      for (int b = 0; b < nbox; ++b)
-        tma_store_4d(&tm, x0, y, b * B, c, tile + (c * nzr + b * B) * TX);
-    bulk_commit();
-    bulk_wait_all();
+      for (int b = 0; b < nbox; ++b) tma_load_4d(buf + (c * nzr + b * B) * TX, &tm, xt * TX, y, b * B, c, bar);
+  };
+  const int tid = threadIdx.x, nth = blockDim.x;
+  if (tid == 0) {
+    mbar_arrive_expect_tx(&full[0], tile_bytes + a.twbz);
+    bulk_load(tw, a.twz, a.twbz, &full[0]);
+    issue(t, buf0, &full[0]);
   }
+  const float two_pi = 6.283185307179586f;
+  const int ns = a.az.ns;
+  for (int i = 0, b = 0; t < ntiles; ++i, t += gridDim.x, b = (b + 1 == nbuf) ? 0 : b + 1) {
+    float2* cur = buf0 + b * tileN;
+    const int bn = (b + 1 == nbuf) ? 0 : b + 1;
+    float2* nxb = buf0 + bn * tileN;
+    uint64_t* nbar = &full[bn];
+    const int tn = t + gridDim.x;
+    if (!block_wait(&full[b], fail, a.err, (uint32_t)((i / nbuf) & 1))) return;
+    auto prefetch = [&] {
+      if (tid == 0 && tn < ntiles) {
+        if (nbuf == 2) bulk_wait_read_all();
+        else bulk_wait_read_1();
+        mbar_arrive_expect_tx(nbar, tile_bytes);
+        issue(tn, nxb, nbar);
+      }
+    };
+    const int xt = t % nxt, y = t / nxt;
+    const int x0 = xt * TX;
+    const float py = two_pi / (float)a.ny * (float)fft_freq(y, a.ny);
+    const float qy = (2 * y == a.ny) ? 0.f : py;
+    float2* P = cols2_stages<false, TX>(cur, cur, scr, 3, cs, a.az, 0, ns - 1, tw, tid, nth, prefetch);
+    {
+      const int4 g = stage_of(a.az, ns - 1);
+      radix_dispatch(g.x, [&](auto Ri) {
+        constexpr int R = decltype(Ri)::value;
+        stage_last_green<R, TX>(P, cur, cs, g, tw, tid, nth, x0, py, qy, a);
+      });
+    }
+    __syncthreads();
+    if (ns == 1) prefetch();
+    cols2_stages<true, TX>(cur, cur, scr, 3, cs, a.az, 0, ns, tw, tid, nth);
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      for (int c = 0; c < 3; ++c)
+        for (int bb = 0; bb < nbox; ++bb) tma_store_4d(&tm, x0, y, bb * B, c, cur + (c * nzr + bb * B) * TX);
+      bulk_commit();
+    }
+  }
+  if (tid == 0) bulk_wait_all();
 }
 
 template <class F>
@@ -133,29 +238,50 @@ cudaError_t with_tx(int tx, F&& f) {
 
 }  // namespace
 
-// tile + scratch + twiddles + 16 bytes for the mbarrier and the failure flag
-size_t ypass_smem(const IterArgs& a) { return (size_t)(a.nyr + a.ny) * a.tx_y * sizeof(float2) + a.twby + 16; }
+// nbuf tiles + scratch + twiddles + mbarriers (8 bytes each) + 8 bytes for the failure flag
+size_t ypass_smem(const IterArgs& a) {
+  return (size_t)(a.nbuf_y * a.nyr + a.ny) * a.tx_y * sizeof(float2) + a.twby + 8 * a.nbuf_y + 8;
+}
 size_t zpass_smem(const IterArgs& a) {
-  return (size_t)(3 * a.nzr + a.nz) * a.tx_z * sizeof(float2) + a.twbz + 16;
+  return (size_t)3 * (a.nbuf_z + 1) * a.nzr * a.tx_z * sizeof(float2) + a.twbz + 8 * a.nbuf_z + 8;
+}
+int ypass_tiles(const IterArgs& a) { return (a.nx + a.tx_y - 1) / a.tx_y * a.nz * 3; }
+int zpass_tiles(const IterArgs& a) { return (a.nx + a.tx_z - 1) / a.tx_z * a.ny; }
+
+// Persistent grids: as many blocks as fit on the device at once (capped by the tile count).
+cudaError_t yz_grid_sizes(IterArgs& a, int sms) {
+  return with_tx(a.tx_y, [&](auto T) {
+    constexpr int TX = decltype(T)::value;
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ypass<TX, false>, kYZThreads, ypass_smem(a));
+    if (e != cudaSuccess) return e;
+    a.grid_y = std::max(1, std::min(ypass_tiles(a), sms * std::max(1, occ)));
+    return with_tx(a.tx_z, [&](auto T2) {
+      constexpr int TZ = decltype(T2)::value;
+      int occz = 0;
+      cudaError_t e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occz, k_zpass_green<TZ>, kYZThreads, zpass_smem(a));
+      if (e2 != cudaSuccess) return e2;
+      a.grid_z = std::max(1, std::min(zpass_tiles(a), sms * std::max(1, occz)));
+      return cudaSuccess;
+    });
+  });
 }
 
 cudaError_t launch_ypass(const CUtensorMap& tm, const IterArgs& a, bool inverse, cudaStream_t s) {
-  dim3 grid((a.nx + a.tx_y - 1) / a.tx_y, a.nz, 3);
   return with_tx(a.tx_y, [&](auto T) {
     constexpr int TX = decltype(T)::value;
     if (inverse)
-      k_ypass<TX, true><<<grid, 256, ypass_smem(a), s>>>(tm, a);
+      k_ypass<TX, true><<<a.grid_y, kYZThreads, ypass_smem(a), s>>>(tm, a);
     else
-      k_ypass<TX, false><<<grid, 256, ypass_smem(a), s>>>(tm, a);
+      k_ypass<TX, false><<<a.grid_y, kYZThreads, ypass_smem(a), s>>>(tm, a);
     return cudaGetLastError();
   });
 }
 
 cudaError_t launch_zpass_green(const CUtensorMap& tm, const IterArgs& a, cudaStream_t s) {
-  dim3 grid((a.nx + a.tx_z - 1) / a.tx_z, a.ny, 1);
   return with_tx(a.tx_z, [&](auto T) {
     constexpr int TX = decltype(T)::value;
-    k_zpass_green<TX><<<grid, 256, zpass_smem(a), s>>>(tm, a);
+    k_zpass_green<TX><<<a.grid_z, kYZThreads, zpass_smem(a), s>>>(tm, a);
     return cudaGetLastError();
   });
 }
