@@ -280,13 +280,30 @@ def run_gpu(args, rank, world, local_rank):
     plan.close()
 
 
+def source_digest():
+    """sha256 over the CUDA sources (kernels, headers), to tell whether measured counters are
+    still those of the code being run."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2506_15411_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
 def load_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it is current."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per launch of `kernel` on this workload from the committed ncu summary
+    (profiles/traffic_fresnel_lens_275x275x315.json), or None when the kernels have changed
+    since those counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic_fresnel_lens_275x275x315.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        v = d.get(kernel)
+        if d.get("source_sha256") != source_digest():
+            return None
+        v = d["bytes_per_launch"].get(kernel)
         return None if v is None else float(v)
     except Exception:
         return None
@@ -295,14 +312,18 @@ def load_traffic(kernel):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--max-iter", type=int, default=200000)
     ap.add_argument("--check-every", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--print-digest", action="store_true", help="print the CUDA source digest and exit")
     args = ap.parse_args()
+    if args.print_digest:
+        print(source_digest())
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
