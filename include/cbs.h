@@ -129,6 +129,10 @@ int cbs_adjoint(cbs_plan_t plan, const int r0[3], const void* E_dev, void* Eadj_
 int cbs_gradient(cbs_plan_t plan, const void* E_dev, const void* Eadj_dev, const int r0[3],
                  float* grad_dev, double* objective);
 
+/* Figure of merit alone: *objective = |E(r0)|^2 (FP64) for a field on the device.
+ * Errors: CBS_ERR_ARG, CBS_ERR_CUDA. */
+int cbs_objective(cbs_plan_t plan, const void* E_dev, const int r0[3], double* objective);
+
 /* One design iteration from HOST buffers: copies eps (float32 [nz][ny][nx]) to the device,
  * sets it, runs the forward solve for *src into a plan-owned field, the adjoint solve for
  * |E(r0)|^2 and the gradient, and copies the gradient back into grad_host (float32

@@ -27,7 +27,7 @@ CBS_SRC_USER = 2
 
 # Every symbol include/cbs.h declares.
 EXPORTS = ("cbs_plan", "cbs_set_permittivity", "cbs_get_splitting", "cbs_set_solver",
-           "cbs_forward", "cbs_adjoint", "cbs_gradient", "cbs_design_step_host",
+           "cbs_forward", "cbs_adjoint", "cbs_gradient", "cbs_objective", "cbs_design_step_host",
            "cbs_set_profiling", "cbs_pass_times", "cbs_splitting_noalloc", "cbs_destroy",
            "cbs_last_error")
 
@@ -71,6 +71,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "cbs_forward": (c_int, [P, POINTER(cbs_source), P, POINTER(cbs_stats)]),
         "cbs_adjoint": (c_int, [P, POINTER(c_int * 3), P, P, POINTER(cbs_stats)]),
         "cbs_gradient": (c_int, [P, P, P, POINTER(c_int * 3), P, POINTER(c_double)]),
+        "cbs_objective": (c_int, [P, P, POINTER(c_int * 3), POINTER(c_double)]),
         "cbs_design_step_host": (c_int, [P, P, POINTER(cbs_source), POINTER(c_int * 3), P,
                                          POINTER(c_double), POINTER(cbs_stats), POINTER(cbs_stats)]),
         "cbs_set_profiling": (c_int, [P, c_int]),

@@ -858,6 +858,20 @@ int cbs_gradient(cbs_plan_t p, const void* E_dev, const void* Eadj_dev, const in
   return CBS_OK;
 }
 
+int cbs_objective(cbs_plan_t p, const void* E_dev, const int r0[3], double* objective) {
+  g_err.clear();
+  if (!p || !E_dev || !r0 || !objective) return fail(CBS_ERR_ARG, "NULL argument");
+  if (r0[0] < 0 || r0[0] >= p->d.nx || r0[1] < 0 || r0[1] >= p->d.ny || r0[2] < 0 || r0[2] >= p->d.nz)
+    return fail(CBS_ERR_ARG, "r0 (%d,%d,%d) outside the grid", r0[0], r0[1], r0[2]);
+  int rc = sync_in(p);
+  if (rc) return rc;
+  CK(launch_objective(static_cast<const float2*>(E_dev), p->N, p->d.nx, p->d.ny, r0[0], r0[1], r0[2], p->dobj,
+                      p->stream));
+  CK(cudaMemcpyAsync(objective, p->dobj, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return CBS_OK;
+}
+
 int cbs_design_step_host(cbs_plan_t p, const float* eps_host, const cbs_source* src, const int r0[3],
                          float* grad_host, double* objective, cbs_stats* fwd, cbs_stats* adj) {
   g_err.clear();

@@ -204,6 +204,14 @@ class CBSPlan:
                                       ctypes.c_void_p(_ptr(grad)), ctypes.byref(obj) if r is not None else None))
         return grad, (obj.value if r0 is not None else None)
 
+    def objective(self, E: torch.Tensor, r0) -> float:
+        """|E(r0)|^2 (FP64 on the device)."""
+        self._check_field(E, "E")
+        r = (ctypes.c_int * 3)(*[int(v) for v in r0])
+        obj = ctypes.c_double()
+        L.check(self.lib.cbs_objective(self.handle, ctypes.c_void_p(_ptr(E)), ctypes.byref(r), ctypes.byref(obj)))
+        return obj.value
+
     def design_step_host(self, eps_host: np.ndarray, source, r0, grad_host: Optional[np.ndarray] = None):
         """Forward + adjoint + gradient from host memory (the library copies in and out).
         Returns (grad_host, objective, fwd Stats, adj Stats)."""
