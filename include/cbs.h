@@ -79,7 +79,10 @@ typedef struct {
   int z_plane;              /* plane-wave sheet; < 0 selects pad_lo[2] */
   int r0[3];                /* point-source voxel (x, y, z) */
   const void* user_src_dev; /* CBS_SRC_USER only */
-  int warm_start;           /* nonzero: E_dev holds the initial guess; else E starts at 0 */
+  int warm_start;           /* 0: E starts at 0.  1: E_dev holds the initial guess; residuals
+                               are relative to this run's first.  2: as 1, but relative to
+                               the first residual of a start from 0 (one extra iteration
+                               computes it), so a good guess stops early. */
 } cbs_source;
 
 /* Outcome of one solve (always filled when the pointer is not NULL). */
@@ -169,6 +172,66 @@ int cbs_pass_times(cbs_plan_t plan, double ms_total[5], long long launches[5], i
  * epsilon = 0), CBS_ERR_CUDA.  Blocks the host until the result is back. */
 int cbs_splitting_noalloc(const cbs_plan_desc* desc, const float* eps_real_dev, double* k0sq,
                           double* epsilon);
+
+/* ---------------------------------------------------------------- inverse design
+ * One gradient step of the lens design loop of Section 3 / Fig. 2(a) on the thickness map
+ * h(x, y) (float32 [ny][nx] on the device, micrometres; x, y the plan's lateral grid):
+ *     h_eff = G_sigma[M h]             M: mirror average over (+-x, +-y) about the grid
+ *                                      centre; G_sigma: separable Gaussian of std sigma,
+ *                                      weights exp(-k^2/2s^2) for |k| <= ceil(4s), s = sigma /
+ *                                      pitch, normalised, zero outside the map
+ *     eps_r = n_bg^2 + f (n_lens^2 - n_bg^2),  f = clamp(h_eff / pitch - (z - z_base), 0, 1)
+ *                                      for z >= z_base, else 0 (shape Theta(h - z) with
+ *                                      subpixel filling along z)
+ *     forward and adjoint CBS, dL/d eps_r = 2 k_vac^2 Re[E_adj . E], L = |E(r0)|^2
+ *     dL/dh = M G_sigma[(n_lens^2 - n_bg^2)/pitch * dL/d eps_r at z_base + floor(h_eff/pitch)]
+ *     Adam (Kingma & Ba) ascent on L with step alpha [um], then 0 <= h <= h_max inside the
+ *     aperture (pixel centre within D/2 of the grid centre) and h = 0 outside it.
+ * A design object belongs to one plan (same device and stream; not thread-safe) and owns
+ * Adam's moments (2 maps), four scratch maps and two volumes (eps_r, dL/d eps_r: 8 B/voxel). */
+typedef struct cbs_design_s* cbs_design_t;
+
+typedef struct {
+  int z_base;           /* z index of the lens base plane (h = 0) */
+  double n_lens;        /* lens index (the background is the plan's n_bg) */
+  double aperture_um;   /* design-region diameter D */
+  double h_max_um;      /* upper bound of h */
+  double sigma_um;      /* Gaussian smoothing std; 0 = none (ceil(4 sigma/pitch) <= 256) */
+  int mirror;           /* nonzero: impose h(x, y) = h(+-x, +-y) */
+  double alpha;         /* Adam step [um] (0.3 in Section 3) */
+  double beta1, beta2;  /* Adam decay rates (0.9, 0.999) */
+  double adam_eps;      /* Adam regulariser (1e-6) */
+} cbs_design_desc;
+
+/* Create / free a design object for plan.  Errors: CBS_ERR_ARG, CBS_ERR_OOM, CBS_ERR_CUDA. */
+int cbs_design_create(cbs_design_t* out, cbs_plan_t plan, const cbs_design_desc* desc);
+void cbs_design_destroy(cbs_design_t design);
+
+/* Zero Adam's moments and step count. */
+int cbs_design_reset(cbs_design_t design);
+
+/* h -> h_eff (into h_eff_dev when not NULL) -> eps_r (float32 [nz][ny][nx] into eps_dev). */
+int cbs_design_permittivity(cbs_design_t design, const float* h_dev, float* h_eff_dev, float* eps_dev);
+
+/* dL/dh (float32 [ny][nx] into grad_h_dev) from dL/d eps_r (float32 [nz][ny][nx]) at the
+ * design h_dev: the surface derivative and the adjoints of G_sigma and M. */
+int cbs_design_height_gradient(cbs_design_t design, const float* h_dev, const float* grad_eps_dev,
+                               float* grad_h_dev);
+
+/* One Adam ascent step on h_dev (in place) for the gradient dL/dh in grad_h_dev, with the
+ * box and aperture constraints; counts one step. */
+int cbs_design_adam(cbs_design_t design, float* h_dev, const float* grad_h_dev);
+
+/* The whole step: eps_r from h_dev, cbs_set_permittivity, the forward solve of *src into
+ * E_dev and the adjoint solve of |E(r0)|^2 into Eadj_dev (both warm-started from their
+ * contents when src->warm_start is 1 or 2, with that meaning), the gradient, dL/dh (copied
+ * into grad_h_dev when not NULL) and the Adam update of h_dev in place.  *objective =
+ * |E(r0)|^2 before the update.  fwd/adj may be NULL.  A solve that ends NOT_CONVERGED or
+ * STAGNATED does not stop the step (its status is in fwd/adj); other errors return at the
+ * failing step, with h_dev not updated. */
+int cbs_design_step(cbs_design_t design, float* h_dev, const cbs_source* src, const int r0[3],
+                    void* E_dev, void* Eadj_dev, float* grad_h_dev, double* objective,
+                    cbs_stats* fwd, cbs_stats* adj);
 
 /* Free the plan and its device memory (NULL is a no-op). */
 void cbs_destroy(cbs_plan_t plan);

@@ -29,7 +29,8 @@ CBS_SRC_USER = 2
 EXPORTS = ("cbs_plan", "cbs_set_permittivity", "cbs_get_splitting", "cbs_set_solver",
            "cbs_forward", "cbs_adjoint", "cbs_gradient", "cbs_objective", "cbs_design_step_host",
            "cbs_set_profiling", "cbs_pass_times", "cbs_splitting_noalloc", "cbs_destroy",
-           "cbs_last_error")
+           "cbs_last_error", "cbs_design_create", "cbs_design_destroy", "cbs_design_reset",
+           "cbs_design_permittivity", "cbs_design_height_gradient", "cbs_design_adam", "cbs_design_step")
 
 PASS_NAMES = ("k_xpass_fwd", "k_ypass_fwd", "k_zpass_green", "k_ypass_inv", "k_xpass_inv_update")
 
@@ -50,6 +51,12 @@ class cbs_source(Structure):
 class cbs_stats(Structure):
     _fields_ = [("iters", c_int), ("rel_resid", c_double), ("resid0", c_double),
                 ("seconds", c_double), ("status", c_int)]
+
+
+class cbs_design_desc(Structure):
+    _fields_ = [("z_base", c_int), ("n_lens", c_double), ("aperture_um", c_double), ("h_max_um", c_double),
+                ("sigma_um", c_double), ("mirror", c_int), ("alpha", c_double), ("beta1", c_double),
+                ("beta2", c_double), ("adam_eps", c_double)]
 
 
 class CBSError(RuntimeError):
@@ -78,6 +85,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "cbs_pass_times": (c_int, [P, POINTER(c_double * 5), POINTER(ctypes.c_longlong * 5), c_int]),
         "cbs_splitting_noalloc": (c_int, [POINTER(cbs_plan_desc), P, POINTER(c_double), POINTER(c_double)]),
         "cbs_destroy": (None, [P]),
+        "cbs_design_create": (c_int, [POINTER(c_void_p), P, POINTER(cbs_design_desc)]),
+        "cbs_design_destroy": (None, [P]),
+        "cbs_design_reset": (c_int, [P]),
+        "cbs_design_permittivity": (c_int, [P, P, P, P]),
+        "cbs_design_height_gradient": (c_int, [P, P, P, P]),
+        "cbs_design_adam": (c_int, [P, P, P]),
+        "cbs_design_step": (c_int, [P, P, POINTER(cbs_source), POINTER(c_int * 3), P, P, P, POINTER(c_double),
+                                    POINTER(cbs_stats), POINTER(cbs_stats)]),
         "cbs_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():

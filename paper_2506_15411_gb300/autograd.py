@@ -23,7 +23,7 @@ class FocalIntensity(torch.autograd.Function):
         eps_c = eps.detach().to(torch.float32).contiguous()
         plan.set_permittivity(eps_c)
         if E_init is not None:
-            E, st = plan.forward(source, E=E_init.detach().clone(), warm_start=True)
+            E, st = plan.forward(source, E=E_init.detach().clone(), warm_start=2)
         else:
             E, st = plan.forward(source)
         r0 = tuple(int(v) for v in r0)
@@ -50,7 +50,8 @@ def focal_intensity(eps: torch.Tensor, plan: CBSPlan, source, r0,
     """|E(r0)|^2 (float64 scalar tensor) for the permittivity eps ((nz, ny, nx) on the plan's
     device), differentiable with respect to eps.
 
-    E_init warm-starts the forward series (the fixed point does not depend on it).  After
+    E_init warm-starts the forward series (the fixed point does not depend on it), with the
+    residual measured against a start from zero, so a close guess stops early.  After
     the call, plan.last_forward / plan.last_field hold the forward Stats and field, and after
     backward plan.last_adjoint the adjoint Stats; a solve that ends NOT_CONVERGED or
     STAGNATED does not raise, so callers that need convergence check those Stats."""

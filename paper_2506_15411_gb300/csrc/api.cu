@@ -27,7 +27,7 @@
 #include <vector>
 
 #include "../../include/cbs.h"
-#include "cbs_internal.h"
+#include "plan.h"
 
 namespace cbs {
 cudaError_t xpass_set_smem_limit(int bytes);
@@ -39,23 +39,6 @@ using namespace cbs;
 namespace {
 
 thread_local std::string g_err;
-
-int fail(int code, const char* fmt, ...) {
-  char buf[512];
-  va_list ap;
-  va_start(ap, fmt);
-  vsnprintf(buf, sizeof(buf), fmt, ap);
-  va_end(ap);
-  g_err = buf;
-  return code;
-}
-
-#define CK(call)                                                                         \
-  do {                                                                                   \
-    cudaError_t e_ = (call);                                                             \
-    if (e_ != cudaSuccess)                                                               \
-      return fail(CBS_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));         \
-  } while (0)
 
 constexpr double kPiD = 3.14159265358979323846;
 constexpr int kMaxN = 1024;
@@ -127,11 +110,6 @@ std::vector<int4> stage_table(const AxisPlan& ap) {
   return t;
 }
 
-int pow2_ceil(int v) {
-  int p = 1;
-  while (p < v) p <<= 1;
-  return p;
-}
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
@@ -166,13 +144,7 @@ bool encode_w_map(CUtensorMap* tm, float2* W, int nx, int ny, int nz, int nxp, i
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// A captured block of iterations bakes in the field pointer and the whole source.
-struct GraphEntry {
-  float2* E;
-  SourceArgs src;
-  int iters;
-  cudaGraphExec_t exec;
-};
+
 
 bool same_source(const SourceArgs& a, const SourceArgs& b) {
   if (a.kind != b.kind || a.zp != b.zp || a.px != b.px || a.py != b.py || a.pz != b.pz ||
@@ -193,56 +165,18 @@ const char* set_last_error(const char* msg) {
 }
 }  // namespace cbs
 
-struct cbs_plan_s {
-  cbs_plan_desc d{};
-  int device = 0;
-  cudaStream_t user_stream = nullptr;
-  cudaStream_t stream = nullptr;   // the caller's stream, or an owned one for NULL (legacy)
-  bool own_stream = false;
-  cudaEvent_t ev = nullptr;
-  CUtensorMap tmy{}, tmz{};        // W maps for the y pass and the z pass
-  int* err_dev = nullptr;          // kernels' error flag
-  int* err_host = nullptr;         // pinned copy
-  IterArgs base{};
-  size_t N = 0;
-  double pitch = 0, kvac = 0;
-  // device memory owned by the plan
-  float2* V = nullptr;
-  float2* W = nullptr;
-  float2* Ei = nullptr;            // the field being iterated, padded rows
-  float2* tw = nullptr;
-  int4* stages = nullptr;
-  double* partials = nullptr;
-  unsigned* counter = nullptr;
-  double* hist = nullptr;
-  float2* adj_amp = nullptr;
-  double* dobj = nullptr;
-  double *sx = nullptr, *sy = nullptr, *sz = nullptr;
-  // set-up scratch
-  float *pmin = nullptr, *pmax = nullptr;
-  int* pbad = nullptr;
-  double* pdev = nullptr;
-  int red_blocks = 0;
-  // host staging (pinned)
-  double* hist_host = nullptr;
-  // host-buffer design step
-  float* eps_dev = nullptr;
-  float2* Ef = nullptr;
-  float2* Ea = nullptr;
-  float* grad_dev = nullptr;
-  // splitting (scaled units)
-  bool have_eps = false;
-  double k0sq_s = 0, eps_s = 0;
-  // graphs of one block of check_every iterations, per (E, source) binding
-  std::vector<GraphEntry> graphs;
-  // pass timing (events around the launches of the last iteration of each block)
-  bool profiling = false;
-  cudaEvent_t pev[6] = {};
-  double pass_ms[5] = {};
-  long long pass_n[5] = {};
-};
 
-namespace {
+namespace cbs {
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
 
 void drop_graphs(cbs_plan_s* p) {
   for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
@@ -363,93 +297,221 @@ int make_source(cbs_plan_s* p, const cbs_source* src, SourceArgs& s) {
   return CBS_OK;
 }
 
-int run_series(cbs_plan_s* p, float2* E, const SourceArgs& src, bool warm, cbs_stats* st) {
-  const auto t0 = std::chrono::steady_clock::now();
-  cbs_stats local{};
-  cbs_stats* S = st ? st : &local;
-  *S = cbs_stats{};
-  if (!p->have_eps) return S->status = fail(CBS_ERR_STATE, "cbs_set_permittivity has not been called");
-  IterArgs a = p->base;
-  a.E = p->Ei;   // iterate on the plan's padded copy; the caller's E is read and written once
-  a.src = src;
+
+size_t dense_row_bytes(const cbs_plan_s* p) { return (size_t)p->d.nx * sizeof(float2); }
+size_t pad_row_bytes(const cbs_plan_s* p) { return (size_t)p->base.nxp * sizeof(float2); }
+size_t field_rows(const cbs_plan_s* p) { return (size_t)3 * p->d.ny * p->d.nz; }
+
+// Enqueue the next block of iterations, the copy of its residual sums and of the error flag,
+// and the event the host waits on.
+int series_enqueue_block(cbs_plan_s* p, SeriesRun& R) {
+  R.m = std::min(p->d.check_every, p->d.max_iter - R.it);
+  // full blocks replay a graph; with profiling the last iteration runs outside it
+  const int ng = (R.m == p->d.check_every) ? (p->profiling ? R.m - 1 : R.m) : 0;
+  bool used = false;
   int rc = CBS_OK;
-  const size_t dense_row = (size_t)p->d.nx * sizeof(float2), pad_row = (size_t)a.nxp * sizeof(float2);
-  const size_t rows = (size_t)3 * p->d.ny * p->d.nz;
-  {
-    cudaError_t e = cudaMemsetAsync(p->Ei, 0, 3 * a.Nw * sizeof(float2), p->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->counter, 0, sizeof(unsigned), p->stream);
-    if (e == cudaSuccess && warm)
-      e = cudaMemcpy2DAsync(p->Ei, pad_row, E, dense_row, dense_row, rows, cudaMemcpyDeviceToDevice, p->stream);
-    if (e != cudaSuccess) return S->status = fail(CBS_ERR_CUDA, "field copy-in: %s", cudaGetErrorString(e));
-  }
-  int it = 0;
-  double r0 = -1.0, rel = 0.0;
-  double best = 1e300;
-  int best_it = 0;
-  bool done = false;
-  while (!done && it < p->d.max_iter) {
-    const int m = std::min(p->d.check_every, p->d.max_iter - it);
-    // full blocks replay a graph; with profiling the last iteration runs outside it
-    const int ng = (m == p->d.check_every) ? (p->profiling ? m - 1 : m) : 0;
-    bool used = false;
-    if (ng > 1) rc = graph_block(p, a, ng, used);
-    if (!rc) rc = launch_range(p, a, used ? ng : 0, m, m);
-    if (rc) break;
-    cudaError_t e = cudaMemcpyAsync(p->hist_host, p->hist, m * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p->err_host, p->err_dev, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
-    if (e != cudaSuccess) {
-      rc = fail(CBS_ERR_CUDA, "iteration block failed: %s", cudaGetErrorString(e));
-      break;
-    }
-    if (*p->err_host) {
-      rc = fail(CBS_ERR_CUDA, "a tensor-copy wait timed out in an FFT pass (device error %d)", *p->err_host);
-      break;
-    }
-    rc = collect_pass_times(p);
-    if (rc) break;
-    for (int k = 0; k < m; ++k) {
-      ++it;
-      const double r = std::sqrt(p->hist_host[k]);
-      if (r0 < 0) r0 = r;
-      rel = r0 > 0 ? r / r0 : 0.0;
-      if (!std::isfinite(r) || rel > 1e4) {
-        rc = fail(CBS_ERR_DIVERGED, "series diverged at iteration %d (relative residual %g)", it, rel);
-        done = true;
-        break;
-      }
-      // a converged iteration inside a block still lets the block finish: `it` counts
-      // every iteration that ran and `rel` is the residual of the last one
-      if (p->d.tol > 0 && rel <= p->d.tol) done = true;
-      if (rel < 0.99 * best) {
-        best = rel;
-        best_it = it;
-      }
-    }
-    // stagnation: the residual has sat at its rounding floor for a long stretch
-    if (!done && !rc && p->d.tol > 0 && it - best_it >= std::max(1000, it / 4)) {
-      rc = fail(CBS_ERR_STAGNATED, "residual stagnated at %g (best %g) after %d iterations, above tol %g",
-                rel, best, it, p->d.tol);
-      done = true;
-    }
-  }
-  {
-    cudaError_t e = cudaMemcpy2DAsync(E, dense_row, p->Ei, pad_row, dense_row, rows, cudaMemcpyDeviceToDevice,
-                                      p->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
-    if (e != cudaSuccess && rc == CBS_OK) rc = fail(CBS_ERR_CUDA, "field copy-out: %s", cudaGetErrorString(e));
-  }
-  S->iters = it;
-  S->rel_resid = rel;
-  S->resid0 = r0 < 0 ? 0.0 : r0;
-  if (rc == CBS_OK && p->d.tol > 0 && !(rel <= p->d.tol))
-    rc = fail(CBS_ERR_NOT_CONVERGED, "relative residual %g > tol %g after %d iterations", rel, p->d.tol, it);
-  S->status = rc;
-  S->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  return rc;
+  if (ng > 1) rc = graph_block(p, R.a, ng, used);
+  if (!rc) rc = launch_range(p, R.a, used ? ng : 0, R.m, R.m);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(p->hist_host, p->hist, R.m * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaMemcpyAsync(p->err_host, p->err_dev, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaEventRecord(p->blk_ev, p->stream));
+  R.iterating = true;
+  return CBS_OK;
 }
 
-}  // namespace
+// Host side of a completed block: error flag, pass times, residuals, stopping rules.
+// Sets R.rc on an error and returns whether iterating is over.
+bool series_absorb_block(cbs_plan_s* p, SeriesRun& R) {
+  R.iterating = false;
+  if (*p->err_host) {
+    R.rc = fail(CBS_ERR_CUDA, "a tensor-copy wait timed out in an FFT pass (device error %d)", *p->err_host);
+    return true;
+  }
+  R.rc = collect_pass_times(p);
+  if (R.rc) return true;
+  bool done = false;
+  for (int k = 0; k < R.m; ++k) {
+    ++R.it;
+    const double r = std::sqrt(p->hist_host[k]);
+    if (R.r0 < 0) R.r0 = r;
+    R.rel = R.r0 > 0 ? r / R.r0 : 0.0;
+    if (!std::isfinite(r) || R.rel > 1e4) {
+      R.rc = fail(CBS_ERR_DIVERGED, "series diverged at iteration %d (relative residual %g)", R.it, R.rel);
+      return true;
+    }
+    // a converged iteration inside a block still lets the block finish: `it` counts every
+    // iteration that ran and `rel` is the residual of the last one
+    if (p->d.tol > 0 && R.rel <= p->d.tol) done = true;
+    if (R.rel < 0.99 * R.best) {
+      R.best = R.rel;
+      R.best_it = R.it;
+    }
+  }
+  // stagnation: the residual has sat at its rounding floor for a long stretch
+  if (!done && p->d.tol > 0 && R.it - R.best_it >= std::max(1000, R.it / 4)) {
+    R.rc = fail(CBS_ERR_STAGNATED, "residual stagnated at %g (best %g) after %d iterations, above tol %g", R.rel,
+                R.best, R.it, p->d.tol);
+    return true;
+  }
+  return done || R.it >= p->d.max_iter;
+}
+
+// Copy the iterate back into the caller's field (also after an error: E then holds the last
+// iterate), with blk_ev marking its end.
+void series_enqueue_copy_out(cbs_plan_s* p, SeriesRun& R) {
+  cudaError_t e = cudaMemcpy2DAsync(R.E, dense_row_bytes(p), p->Ei, pad_row_bytes(p), dense_row_bytes(p),
+                                    field_rows(p), cudaMemcpyDeviceToDevice, p->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(p->blk_ev, p->stream);
+  if (e != cudaSuccess) {
+    if (R.rc == CBS_OK) R.rc = fail(CBS_ERR_CUDA, "field copy-out: %s", cudaGetErrorString(e));
+    R.finished = true;
+    return;
+  }
+  R.copying = true;
+}
+
+// Start a run: zero the iterate (and copy in the warm start), enqueue the first block.
+// warm: 0 = start from E = 0; 1 = start from E, residuals relative to this run's first;
+// 2 = start from E, residuals relative to the first residual of a start from 0 (one extra
+// iteration from zero computes it, so a warm start converges in fewer iterations; that
+// iteration is waited for here).  On an error before the first block R.finished is set.
+void series_begin(cbs_plan_s* p, float2* E, const SourceArgs& src, int warm, SeriesRun& R) {
+  R = SeriesRun{};
+  R.t0 = std::chrono::steady_clock::now();
+  R.E = E;
+  if (!p->have_eps) {
+    R.rc = fail(CBS_ERR_STATE, "cbs_set_permittivity has not been called");
+    R.finished = true;
+    return;
+  }
+  R.a = p->base;
+  R.a.E = p->Ei;   // iterate on the plan's padded copy; the caller's E is read and written once
+  R.a.src = src;
+  cudaError_t e = cudaMemsetAsync(p->Ei, 0, 3 * R.a.Nw * sizeof(float2), p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->counter, 0, sizeof(unsigned), p->stream);
+  if (e != cudaSuccess) {
+    R.rc = fail(CBS_ERR_CUDA, "field set-up: %s", cudaGetErrorString(e));
+    R.finished = true;
+    return;
+  }
+  if (warm == 2) {
+    IterArgs a1 = R.a;
+    a1.slot = 0;
+    int rc = launch_iteration(p, a1, p->stream, nullptr);
+    if (!rc) {
+      e = cudaMemcpyAsync(p->hist_host, p->hist, sizeof(double), cudaMemcpyDeviceToHost, p->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(p->err_host, p->err_dev, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+      if (e != cudaSuccess)
+        rc = fail(CBS_ERR_CUDA, "reference iteration: %s", cudaGetErrorString(e));
+      else if (*p->err_host)
+        rc = fail(CBS_ERR_CUDA, "a tensor-copy wait timed out in an FFT pass (device error %d)", *p->err_host);
+    }
+    if (rc) {
+      R.rc = rc;
+      R.finished = true;
+      return;
+    }
+    R.r0 = std::sqrt(p->hist_host[0]);
+    if (!(R.r0 > 0.0)) R.r0 = -1.0;   // a zero source: fall back to this run's first residual
+    e = cudaMemsetAsync(p->Ei, 0, 3 * R.a.Nw * sizeof(float2), p->stream);
+  }
+  if (warm && e == cudaSuccess)
+    e = cudaMemcpy2DAsync(p->Ei, pad_row_bytes(p), E, dense_row_bytes(p), dense_row_bytes(p), field_rows(p),
+                          cudaMemcpyDeviceToDevice, p->stream);
+  if (e != cudaSuccess) {
+    R.rc = fail(CBS_ERR_CUDA, "field copy-in: %s", cudaGetErrorString(e));
+    R.finished = true;
+    return;
+  }
+  R.rc = series_enqueue_block(p, R);
+  if (R.rc) series_enqueue_copy_out(p, R);
+}
+
+// Advance a run: with wait, block until its current block (or copy-out) is done; without,
+// return at once if it is still running.  Returns R.finished.
+bool series_advance(cbs_plan_s* p, SeriesRun& R, bool wait) {
+  if (R.finished) return true;
+  cudaError_t e = wait ? cudaEventSynchronize(p->blk_ev) : cudaEventQuery(p->blk_ev);
+  if (e == cudaErrorNotReady) return false;
+  if (e != cudaSuccess) {
+    if (R.rc == CBS_OK)
+      R.rc = fail(CBS_ERR_CUDA, "%s failed: %s", R.copying ? "field copy-out" : "iteration block",
+                  cudaGetErrorString(e));
+    R.iterating = false;
+    if (!R.copying) {
+      series_enqueue_copy_out(p, R);
+      return R.finished;
+    }
+    R.copying = false;
+    R.finished = true;
+    return true;
+  }
+  if (R.copying) {
+    R.copying = false;
+    R.finished = true;
+    return true;
+  }
+  if (!series_absorb_block(p, R)) {
+    R.rc = series_enqueue_block(p, R);
+    if (R.rc == CBS_OK) return false;
+  }
+  series_enqueue_copy_out(p, R);
+  return R.finished;
+}
+
+// Outcome of a finished run (NOT_CONVERGED when tol > 0 was not reached without another error).
+int series_stats(const cbs_plan_s* p, SeriesRun& R, cbs_stats* S) {
+  if (R.rc == CBS_OK && p->d.tol > 0 && !(R.rel <= p->d.tol))
+    R.rc = fail(CBS_ERR_NOT_CONVERGED, "relative residual %g > tol %g after %d iterations", R.rel, p->d.tol, R.it);
+  if (S) {
+    S->iters = R.it;
+    S->rel_resid = R.rel;
+    S->resid0 = R.r0 < 0 ? 0.0 : R.r0;
+    S->status = R.rc;
+    S->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - R.t0).count();
+  }
+  return R.rc;
+}
+
+int run_series(cbs_plan_s* p, float2* E, const SourceArgs& src, int warm, cbs_stats* st) {
+  if (st) *st = cbs_stats{};
+  SeriesRun R;
+  series_begin(p, E, src, warm, R);
+  while (!series_advance(p, R, true)) {
+  }
+  return series_stats(p, R, st);
+}
+
+int adjoint_source(cbs_plan_s* p, const int r0[3], const void* E_dev, SourceArgs& s) {
+  if (r0[0] < 0 || r0[0] >= p->d.nx || r0[1] < 0 || r0[1] >= p->d.ny || r0[2] < 0 || r0[2] >= p->d.nz)
+    return fail(CBS_ERR_ARG, "r0 (%d,%d,%d) outside the grid", r0[0], r0[1], r0[2]);
+  CK(launch_adjoint_amp(static_cast<const float2*>(E_dev), p->N, p->d.nx, p->d.ny, r0[0], r0[1], r0[2],
+                        (float)(p->pitch * p->pitch), p->adj_amp, p->stream));
+  s = SourceArgs{};
+  s.kind = CBS_SRC_POINT;
+  s.px = r0[0];
+  s.py = r0[1];
+  s.pz = r0[2];
+  s.amp_dev = p->adj_amp;
+  return CBS_OK;
+}
+
+// Adjoint series of |E(r0)|^2 (source conj(E(r0)) at r0); warm as for run_series.
+int adjoint_run(cbs_plan_s* p, const int r0[3], const void* E_dev, void* Eadj_dev, int warm, cbs_stats* stats) {
+  if (stats) *stats = cbs_stats{};
+  int rc = (!p || !r0 || !E_dev || !Eadj_dev) ? fail(CBS_ERR_ARG, "NULL argument") : sync_in(p);
+  SourceArgs s;
+  if (!rc) rc = adjoint_source(p, r0, E_dev, s);
+  if (rc) {
+    if (stats) stats->status = rc;
+    return rc;
+  }
+  return run_series(p, static_cast<float2*>(Eadj_dev), s, warm, stats);
+}
+
+}  // namespace cbs
 
 extern "C" {
 
@@ -504,6 +566,7 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
     p->own_stream = true;         // the legacy stream cannot be captured
   }
   CKP(cudaEventCreateWithFlags(&p->ev, cudaEventDisableTiming));
+  CKP(cudaEventCreateWithFlags(&p->blk_ev, cudaEventDisableTiming));
   CKP(xpass_set_smem_limit(227 * 1024));
   CKP(yzpass_set_smem_limit(227 * 1024));
 
@@ -621,6 +684,7 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
   {
     int sms = 0;
     CKP(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+    p->sms = sms;
     CKP(x_grid_size(a, sms));
     CKP(yz_grid_sizes(a, sms));
   }
@@ -683,6 +747,7 @@ void cbs_destroy(cbs_plan_t p) {
   if (p->hist_host) cudaFreeHost(p->hist_host);
   if (p->err_host) cudaFreeHost(p->err_host);
   if (p->ev) cudaEventDestroy(p->ev);
+  if (p->blk_ev) cudaEventDestroy(p->blk_ev);
   for (cudaEvent_t e : p->pev)
     if (e) cudaEventDestroy(e);
   if (p->stream && p->own_stream) cudaStreamDestroy(p->stream);
@@ -804,6 +869,10 @@ int cbs_forward(cbs_plan_t p, const cbs_source* src, void* E_dev, cbs_stats* sta
     if (stats) stats->status = CBS_ERR_ARG;
     return fail(CBS_ERR_ARG, "NULL argument");
   }
+  if (src->warm_start < 0 || src->warm_start > 2) {
+    if (stats) stats->status = CBS_ERR_ARG;
+    return fail(CBS_ERR_ARG, "warm_start %d is not 0, 1 or 2", src->warm_start);
+  }
   SourceArgs s;
   int rc = make_source(p, src, s);
   if (!rc) rc = sync_in(p);
@@ -811,31 +880,12 @@ int cbs_forward(cbs_plan_t p, const cbs_source* src, void* E_dev, cbs_stats* sta
     if (stats) stats->status = rc;
     return rc;
   }
-  return run_series(p, static_cast<float2*>(E_dev), s, src->warm_start != 0, stats);
+  return run_series(p, static_cast<float2*>(E_dev), s, src->warm_start, stats);
 }
 
 int cbs_adjoint(cbs_plan_t p, const int r0[3], const void* E_dev, void* Eadj_dev, cbs_stats* stats) {
   g_err.clear();
-  if (stats) *stats = cbs_stats{};
-  if (!p || !r0 || !E_dev || !Eadj_dev) {
-    if (stats) stats->status = CBS_ERR_ARG;
-    return fail(CBS_ERR_ARG, "NULL argument");
-  }
-  if (r0[0] < 0 || r0[0] >= p->d.nx || r0[1] < 0 || r0[1] >= p->d.ny || r0[2] < 0 || r0[2] >= p->d.nz) {
-    if (stats) stats->status = CBS_ERR_ARG;
-    return fail(CBS_ERR_ARG, "r0 (%d,%d,%d) outside the grid", r0[0], r0[1], r0[2]);
-  }
-  int rc = sync_in(p);
-  if (rc) return rc;
-  CK(launch_adjoint_amp(static_cast<const float2*>(E_dev), p->N, p->d.nx, p->d.ny, r0[0], r0[1], r0[2],
-                        (float)(p->pitch * p->pitch), p->adj_amp, p->stream));
-  SourceArgs s{};
-  s.kind = CBS_SRC_POINT;
-  s.px = r0[0];
-  s.py = r0[1];
-  s.pz = r0[2];
-  s.amp_dev = p->adj_amp;
-  return run_series(p, static_cast<float2*>(Eadj_dev), s, false, stats);
+  return adjoint_run(p, r0, E_dev, Eadj_dev, 0, stats);
 }
 
 int cbs_gradient(cbs_plan_t p, const void* E_dev, const void* Eadj_dev, const int r0[3], float* grad_dev,
@@ -898,6 +948,234 @@ int cbs_design_step_host(cbs_plan_t p, const float* eps_host, const cbs_source* 
   rc = cbs_gradient(p, p->Ef, p->Ea, r0, p->grad_dev, objective);
   if (rc) return rc;
   CK(cudaMemcpyAsync(grad_host, p->grad_dev, N * sizeof(float), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return CBS_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ inverse design
+struct cbs_design_s {
+  cbs_plan_s* p = nullptr;
+  cbs_design_desc d{};
+  int nx = 0, ny = 0;
+  double pitch_um = 0;
+  int R = 0;                          // Gaussian half-width (0: no smoothing)
+  float* w = nullptr;                 // 2R+1 weights
+  float *t1 = nullptr, *t2 = nullptr, *heff = nullptr, *gh = nullptr, *m = nullptr, *v = nullptr;
+  float *eps = nullptr, *grad = nullptr;
+  int t = 0;                          // Adam steps taken
+};
+
+namespace {
+
+int design_effective(cbs_design_s* D, const float* h, float* out) {
+  cbs_plan_s* p = D->p;
+  const size_t mb = (size_t)D->nx * D->ny * sizeof(float);
+  const float* src = h;
+  if (D->d.mirror) {
+    CK(launch_mirror(h, D->t1, D->nx, D->ny, p->stream));
+    src = D->t1;
+  }
+  if (D->R > 0) {
+    CK(launch_filter(src, D->t2, D->nx, D->ny, D->w, D->R, 0, p->stream));
+    CK(launch_filter(D->t2, out, D->nx, D->ny, D->w, D->R, 1, p->stream));
+  } else if (src != out) {
+    CK(cudaMemcpyAsync(out, src, mb, cudaMemcpyDeviceToDevice, p->stream));
+  }
+  return CBS_OK;
+}
+
+int design_permittivity(cbs_design_s* D, const float* heff, float* eps) {
+  cbs_plan_s* p = D->p;
+  const double eb = p->d.n_bg * p->d.n_bg, el = D->d.n_lens * D->d.n_lens;
+  CK(launch_height_to_eps(heff, eps, D->nx, D->ny, p->d.nz, D->d.z_base, (float)(1.0 / D->pitch_um), (float)eb,
+                          (float)(el - eb), p->sms, p->stream));
+  return CBS_OK;
+}
+
+int design_height_gradient(cbs_design_s* D, const float* heff, const float* grad_eps, float* out) {
+  cbs_plan_s* p = D->p;
+  const double eb = p->d.n_bg * p->d.n_bg, el = D->d.n_lens * D->d.n_lens;
+  const size_t mb = (size_t)D->nx * D->ny * sizeof(float);
+  CK(launch_surface_grad(grad_eps, heff, D->t1, D->nx, D->ny, p->d.nz, D->d.z_base, (float)(1.0 / D->pitch_um),
+                         (float)((el - eb) / D->pitch_um), p->stream));
+  if (D->R > 0) {
+    CK(launch_filter(D->t1, D->t2, D->nx, D->ny, D->w, D->R, 0, p->stream));
+    CK(launch_filter(D->t2, D->t1, D->nx, D->ny, D->w, D->R, 1, p->stream));
+  }
+  if (D->d.mirror)
+    CK(launch_mirror(D->t1, out, D->nx, D->ny, p->stream));
+  else
+    CK(cudaMemcpyAsync(out, D->t1, mb, cudaMemcpyDeviceToDevice, p->stream));
+  return CBS_OK;
+}
+
+int design_adam(cbs_design_s* D, float* h, const float* gh) {
+  cbs_plan_s* p = D->p;
+  D->t += 1;
+  const double c1 = 1.0 / (1.0 - std::pow(D->d.beta1, D->t));
+  const double c2 = 1.0 / (1.0 - std::pow(D->d.beta2, D->t));
+  const double r = 0.5 * D->d.aperture_um;
+  CK(launch_adam(h, gh, D->m, D->v, D->nx, D->ny, D->pitch_um, r * r, (float)D->d.alpha, (float)D->d.beta1,
+                 (float)D->d.beta2, (float)c1, (float)c2, (float)D->d.adam_eps, (float)D->d.h_max_um, p->stream));
+  return CBS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cbs_design_create(cbs_design_t* out, cbs_plan_t p, const cbs_design_desc* desc) {
+  g_err.clear();
+  if (!out || !p || !desc) return fail(CBS_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  const cbs_design_desc& d = *desc;
+  if (d.z_base < 0 || d.z_base >= p->d.nz) return fail(CBS_ERR_ARG, "z_base %d outside the grid", d.z_base);
+  if (!(d.n_lens > 0) || !(d.aperture_um >= 0) || !(d.h_max_um >= 0) || !(d.sigma_um >= 0) || !(d.alpha > 0) ||
+      !(d.beta1 >= 0 && d.beta1 < 1) || !(d.beta2 >= 0 && d.beta2 < 1) || !(d.adam_eps > 0))
+    return fail(CBS_ERR_ARG, "design parameters out of range");
+  auto* D = new cbs_design_s;
+  D->p = p;
+  D->d = d;
+  D->nx = p->d.nx;
+  D->ny = p->d.ny;
+  D->pitch_um = p->d.pitch_m * 1e6;
+  auto bail = [&](int rc) {
+    cbs_design_destroy(D);
+    return rc;
+  };
+  if (d.sigma_um > 0) {
+    const double s = d.sigma_um / D->pitch_um;
+    D->R = (int)std::ceil(4.0 * s);
+    if (D->R > 256) {
+      fail(CBS_ERR_ARG, "smoothing sigma of %g pixels: the filter half-width ceil(4 sigma) exceeds 256", s);
+      return bail(CBS_ERR_ARG);
+    }
+  }
+  const size_t M = (size_t)D->nx * D->ny;
+  cudaError_t e = cudaSetDevice(p->device);
+  for (float** q : {&D->t1, &D->t2, &D->heff, &D->gh, &D->m, &D->v})
+    if (e == cudaSuccess) e = cudaMalloc(q, M * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&D->eps, p->N * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&D->grad, p->N * sizeof(float));
+  if (e == cudaSuccess && D->R > 0) {
+    // w_0 .. w_R of the symmetric kernel exp(-k^2 / 2 s^2), |k| <= R, normalised to sum 1
+    std::vector<double> wd(D->R + 1);
+    const double s = d.sigma_um / D->pitch_um;
+    double sum = 0;
+    for (int k = 0; k <= D->R; ++k) {
+      wd[k] = std::exp(-(double)k * k / (2.0 * s * s));
+      sum += (k == 0 ? 1.0 : 2.0) * wd[k];
+    }
+    std::vector<float> wf(wd.size());
+    for (size_t i = 0; i < wd.size(); ++i) wf[i] = (float)(wd[i] / sum);
+    e = cudaMalloc(&D->w, wf.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(D->w, wf.data(), wf.size() * sizeof(float), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) e = cudaMemset(D->m, 0, M * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(D->v, 0, M * sizeof(float));
+  if (e != cudaSuccess) {
+    fail(e == cudaErrorMemoryAllocation ? CBS_ERR_OOM : CBS_ERR_CUDA, "design set-up: %s", cudaGetErrorString(e));
+    return bail(e == cudaErrorMemoryAllocation ? CBS_ERR_OOM : CBS_ERR_CUDA);
+  }
+  *out = D;
+  return CBS_OK;
+}
+
+void cbs_design_destroy(cbs_design_t D) {
+  if (!D) return;
+  cudaSetDevice(D->p->device);
+  if (D->p->stream) cudaStreamSynchronize(D->p->stream);
+  for (float* q : {D->w, D->t1, D->t2, D->heff, D->gh, D->m, D->v, D->eps, D->grad})
+    if (q) cudaFree(q);
+  delete D;
+}
+
+int cbs_design_reset(cbs_design_t D) {
+  g_err.clear();
+  if (!D) return fail(CBS_ERR_ARG, "NULL argument");
+  int rc = sync_in(D->p);
+  if (rc) return rc;
+  const size_t mb = (size_t)D->nx * D->ny * sizeof(float);
+  CK(cudaMemsetAsync(D->m, 0, mb, D->p->stream));
+  CK(cudaMemsetAsync(D->v, 0, mb, D->p->stream));
+  CK(cudaStreamSynchronize(D->p->stream));
+  D->t = 0;
+  return CBS_OK;
+}
+
+int cbs_design_permittivity(cbs_design_t D, const float* h_dev, float* h_eff_dev, float* eps_dev) {
+  g_err.clear();
+  if (!D || !h_dev || !eps_dev) return fail(CBS_ERR_ARG, "NULL argument");
+  int rc = sync_in(D->p);
+  if (rc) return rc;
+  float* heff = h_eff_dev ? h_eff_dev : D->heff;
+  rc = design_effective(D, h_dev, heff);
+  if (!rc) rc = design_permittivity(D, heff, eps_dev);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(D->p->stream));
+  return CBS_OK;
+}
+
+int cbs_design_height_gradient(cbs_design_t D, const float* h_dev, const float* grad_eps_dev, float* grad_h_dev) {
+  g_err.clear();
+  if (!D || !h_dev || !grad_eps_dev || !grad_h_dev) return fail(CBS_ERR_ARG, "NULL argument");
+  int rc = sync_in(D->p);
+  if (rc) return rc;
+  rc = design_effective(D, h_dev, D->heff);
+  if (!rc) rc = design_height_gradient(D, D->heff, grad_eps_dev, grad_h_dev);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(D->p->stream));
+  return CBS_OK;
+}
+
+int cbs_design_adam(cbs_design_t D, float* h_dev, const float* grad_h_dev) {
+  g_err.clear();
+  if (!D || !h_dev || !grad_h_dev) return fail(CBS_ERR_ARG, "NULL argument");
+  int rc = sync_in(D->p);
+  if (!rc) rc = design_adam(D, h_dev, grad_h_dev);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(D->p->stream));
+  return CBS_OK;
+}
+
+int cbs_design_step(cbs_design_t D, float* h_dev, const cbs_source* src, const int r0[3], void* E_dev,
+                    void* Eadj_dev, float* grad_h_dev, double* objective, cbs_stats* fwd, cbs_stats* adj) {
+  g_err.clear();
+  if (fwd) *fwd = cbs_stats{};
+  if (adj) *adj = cbs_stats{};
+  if (!D || !h_dev || !src || !r0 || !E_dev || !Eadj_dev || !objective) return fail(CBS_ERR_ARG, "NULL argument");
+  if (src->warm_start < 0 || src->warm_start > 2) return fail(CBS_ERR_ARG, "warm_start %d is not 0, 1 or 2", src->warm_start);
+  cbs_plan_s* p = D->p;
+  int rc = sync_in(p);
+  if (!rc) rc = design_effective(D, h_dev, D->heff);
+  if (!rc) rc = design_permittivity(D, D->heff, D->eps);
+  if (rc) return rc;
+  rc = cbs_set_permittivity(p, D->eps);
+  if (rc) return rc;
+  SourceArgs s;
+  rc = make_source(p, src, s);
+  if (rc) return rc;
+  cbs_stats f{}, a{};
+  rc = run_series(p, static_cast<float2*>(E_dev), s, src->warm_start, &f);
+  if (fwd) *fwd = f;
+  if (rc && rc != CBS_ERR_NOT_CONVERGED && rc != CBS_ERR_STAGNATED) return rc;
+  rc = adjoint_run(p, r0, E_dev, Eadj_dev, src->warm_start, &a);
+  if (adj) *adj = a;
+  if (rc && rc != CBS_ERR_NOT_CONVERGED && rc != CBS_ERR_STAGNATED) return rc;
+  const float coef = (float)(2.0 * p->kvac * p->kvac);
+  CK(launch_gradient(static_cast<const float2*>(E_dev), static_cast<const float2*>(Eadj_dev), p->N, coef, D->grad,
+                     p->stream));
+  CK(launch_objective(static_cast<const float2*>(E_dev), p->N, p->d.nx, p->d.ny, r0[0], r0[1], r0[2], p->dobj,
+                      p->stream));
+  rc = design_height_gradient(D, D->heff, D->grad, D->gh);
+  if (!rc && grad_h_dev)
+    CK(cudaMemcpyAsync(grad_h_dev, D->gh, (size_t)D->nx * D->ny * sizeof(float), cudaMemcpyDeviceToDevice,
+                       p->stream));
+  if (!rc) rc = design_adam(D, h_dev, D->gh);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(objective, p->dobj, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
   CK(cudaStreamSynchronize(p->stream));
   return CBS_OK;
 }

@@ -82,7 +82,7 @@ int xpass_tiles(const IterArgs& a);
 cudaError_t yz_grid_sizes(IterArgs& a, int sms);   // sets grid_y, grid_z
 cudaError_t x_grid_size(IterArgs& a, int sms);     // sets grid_x, grid_xf
 
-// Set-up and gradient kernels (cbs_misc.cu).
+// Set-up and gradient kernels (misc.cu).
 cudaError_t launch_eps_minmax(const float* eps, size_t N, float* part_min, float* part_max,
                               int* part_bad, int blocks, cudaStream_t s);
 cudaError_t launch_k2_maxdev(const float* eps, int nx, int ny, int nz, const double* sx,
@@ -97,5 +97,17 @@ cudaError_t launch_gradient(const float2* E, const float2* Ea, size_t N, float c
                             cudaStream_t s);
 cudaError_t launch_objective(const float2* E, size_t N, int nx, int ny, int x, int y, int z,
                              double* out, cudaStream_t s);
+
+// Inverse-design kernels on the thickness map (design.cu).
+cudaError_t launch_mirror(const float* in, float* out, int nx, int ny, cudaStream_t s);
+cudaError_t launch_filter(const float* in, float* out, int nx, int ny, const float* w, int R, int axis,
+                          cudaStream_t s);
+cudaError_t launch_height_to_eps(const float* heff, float* eps, int nx, int ny, int nz, int z_base, float inv_pitch,
+                                 float eb, float de, int sms, cudaStream_t s);
+cudaError_t launch_surface_grad(const float* g, const float* heff, float* out, int nx, int ny, int nz, int z_base,
+                                float inv_pitch, float slope, cudaStream_t s);
+cudaError_t launch_adam(float* h, const float* gh, float* m, float* v, int nx, int ny, double pitch_um,
+                        double r2max, float alpha, float b1, float b2, float c1, float c2, float aeps, float hmax,
+                        cudaStream_t s);
 
 }  // namespace cbs

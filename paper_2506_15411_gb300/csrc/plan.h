@@ -1,0 +1,117 @@
+// plan.h -- the plan object behind cbs_plan_t and the host-side series driver, shared by
+// the C ABI (api.cu) and the request server (serve.cu).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <vector>
+
+#include "../../include/cbs.h"
+#include "cbs_internal.h"
+
+namespace cbs {
+
+// Record a message for cbs_last_error (this thread) and return code.
+int fail(int code, const char* fmt, ...);
+
+}  // namespace cbs
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return cbs::fail(CBS_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));         \
+  } while (0)
+
+namespace cbs {
+
+// A captured block of iterations bakes in the field pointer and the whole source.
+struct GraphEntry {
+  float2* E;
+  SourceArgs src;
+  int iters;
+  cudaGraphExec_t exec;
+};
+
+}  // namespace cbs
+
+struct cbs_plan_s {
+  cbs_plan_desc d{};
+  int device = 0;
+  cudaStream_t user_stream = nullptr;
+  cudaStream_t stream = nullptr;   // the caller's stream, or an owned one for NULL (legacy)
+  bool own_stream = false;
+  cudaEvent_t ev = nullptr;
+  cudaEvent_t blk_ev = nullptr;    // end of the last enqueued block of iterations or copy-out
+  CUtensorMap tmy{}, tmz{};        // W maps for the y pass and the z pass
+  int* err_dev = nullptr;          // kernels' error flag
+  int* err_host = nullptr;         // pinned copy
+  cbs::IterArgs base{};
+  size_t N = 0;
+  double pitch = 0, kvac = 0;
+  int sms = 0;
+  // device memory owned by the plan
+  float2* V = nullptr;
+  float2* W = nullptr;
+  float2* Ei = nullptr;            // the field being iterated, padded rows
+  float2* tw = nullptr;
+  int4* stages = nullptr;
+  double* partials = nullptr;
+  unsigned* counter = nullptr;
+  double* hist = nullptr;
+  float2* adj_amp = nullptr;
+  double* dobj = nullptr;
+  double *sx = nullptr, *sy = nullptr, *sz = nullptr;
+  // set-up scratch
+  float *pmin = nullptr, *pmax = nullptr;
+  int* pbad = nullptr;
+  double* pdev = nullptr;
+  int red_blocks = 0;
+  // host staging (pinned)
+  double* hist_host = nullptr;
+  // host-buffer design step
+  float* eps_dev = nullptr;
+  float2* Ef = nullptr;
+  float2* Ea = nullptr;
+  float* grad_dev = nullptr;
+  // splitting (scaled units)
+  bool have_eps = false;
+  double k0sq_s = 0, eps_s = 0;
+  // graphs of one block of check_every iterations, per (E, source) binding
+  std::vector<cbs::GraphEntry> graphs;
+  // pass timing (events around the launches of the last iteration of each block)
+  bool profiling = false;
+  cudaEvent_t pev[6] = {};
+  double pass_ms[5] = {};
+  long long pass_n[5] = {};
+};
+
+namespace cbs {
+
+// One run of the series on a plan, advanced a block of check_every iterations at a time, so
+// that a caller can keep several plans' runs in flight on their own streams (the server) or
+// wait on one (the blocking calls).
+struct SeriesRun {
+  float2* E = nullptr;     // caller's field: copied in (warm start) and out once
+  IterArgs a{};
+  int it = 0, best_it = 0, m = 0;
+  double r0 = -1.0, rel = 0.0, best = 1e300;
+  int rc = CBS_OK;
+  bool iterating = false;  // a block is in flight (blk_ev marks its residuals on the host)
+  bool copying = false;    // the copy-out is in flight (blk_ev marks its end)
+  bool finished = false;
+  std::chrono::steady_clock::time_point t0;
+};
+
+// Series driver (api.cu).
+int sync_in(cbs_plan_s* p);
+int make_source(cbs_plan_s* p, const cbs_source* src, SourceArgs& s);
+void series_begin(cbs_plan_s* p, float2* E, const SourceArgs& src, int warm, SeriesRun& R);
+bool series_advance(cbs_plan_s* p, SeriesRun& R, bool wait);
+int series_stats(const cbs_plan_s* p, SeriesRun& R, cbs_stats* S);
+int run_series(cbs_plan_s* p, float2* E, const SourceArgs& src, int warm, cbs_stats* st);
+// Source of the adjoint of |E(r0)|^2 (enqueues the read of conj(E(r0)) on the plan's stream).
+int adjoint_source(cbs_plan_s* p, const int r0[3], const void* E_dev, SourceArgs& s);
+
+}  // namespace cbs

@@ -140,7 +140,7 @@ class CBSPlan:
     # -- solves ----------------------------------------------------------------------------
     def _source(self, src, warm: bool) -> L.cbs_source:
         s = L.cbs_source()
-        s.warm_start = 1 if warm else 0
+        s.warm_start = int(warm)
         s.z_plane = -1
         if isinstance(src, PlaneWave):
             s.kind = L.CBS_SRC_PLANE_WAVE
@@ -164,15 +164,17 @@ class CBSPlan:
             s.pol[i][1] = p.imag
         return s
 
-    def forward(self, source, E: Optional[torch.Tensor] = None, warm_start: bool = False):
-        """Solve for the field of `source`; returns (E, Stats).  Raises on errors other than
-        'not converged' and 'stagnated' (then Stats.status says which)."""
+    def forward(self, source, E: Optional[torch.Tensor] = None, warm_start: int = 0):
+        """Solve for the field of `source`; returns (E, Stats).  warm_start: 0 starts from
+        zero; 1 from E with residuals relative to this run's first; 2 from E with residuals
+        relative to a start from zero (stops early for a close guess).  Raises on errors
+        other than 'not converged' and 'stagnated' (then Stats.status says which)."""
         if E is None:
             if warm_start:
                 raise ValueError("warm_start needs E")
             E = _field_like(self.shape, self.device)
         self._check_field(E, "E")
-        s = self._source(source, warm_start)
+        s = self._source(source, int(warm_start))
         st = L.cbs_stats()
         L.check(self.lib.cbs_forward(self.handle, ctypes.byref(s), ctypes.c_void_p(_ptr(E)),
                                      ctypes.byref(st)), allow=(L.CBS_OK, L.CBS_ERR_NOT_CONVERGED, L.CBS_ERR_STAGNATED))

@@ -44,11 +44,15 @@ int main(void) {
   printf("cbs_plan_desc size %zu\n", sizeof(cbs_plan_desc));
   printf("cbs_source size %zu\n", sizeof(cbs_source));
   printf("cbs_stats size %zu\n", sizeof(cbs_stats));
+  printf("cbs_design_desc size %zu\n", sizeof(cbs_design_desc));
   F(cbs_plan_desc, pitch_m); F(cbs_plan_desc, pad_lo); F(cbs_plan_desc, pad_hi); F(cbs_plan_desc, tol);
   F(cbs_plan_desc, max_iter); F(cbs_plan_desc, check_every); F(cbs_plan_desc, cuda_stream);
   F(cbs_source, pol); F(cbs_source, z_plane); F(cbs_source, r0); F(cbs_source, user_src_dev);
   F(cbs_source, warm_start);
   F(cbs_stats, rel_resid); F(cbs_stats, resid0); F(cbs_stats, seconds); F(cbs_stats, status);
+  F(cbs_design_desc, n_lens); F(cbs_design_desc, aperture_um); F(cbs_design_desc, h_max_um);
+  F(cbs_design_desc, sigma_um); F(cbs_design_desc, mirror); F(cbs_design_desc, alpha);
+  F(cbs_design_desc, beta1); F(cbs_design_desc, beta2); F(cbs_design_desc, adam_eps);
   return 0;
 }
 ''')
@@ -60,7 +64,8 @@ int main(void) {
         if ln:
             t, m, v = ln.split()
             got[(t, m)] = int(v)
-    types = {"cbs_plan_desc": L.cbs_plan_desc, "cbs_source": L.cbs_source, "cbs_stats": L.cbs_stats}
+    types = {"cbs_plan_desc": L.cbs_plan_desc, "cbs_source": L.cbs_source, "cbs_stats": L.cbs_stats,
+             "cbs_design_desc": L.cbs_design_desc}
     for (t, m), v in got.items():
         if m == "size":
             assert ctypes.sizeof(types[t]) == v, (t, v)

@@ -137,13 +137,13 @@ def test_autograd_design_volume_directional_difference():
         d = np.where(mask, g, 0.0) / np.abs(g[mask]).max()
         slope = float(np.sum(g * d))
         L0 = L.item()
-        h = 0.02 * L0 / abs(slope)      # moves L by about 2 % each way
-        assert h <= 0.05, h
+        h = 0.05 * L0 / abs(slope)      # moves L by about 5 % each way
+        assert h <= 0.1, h
         dd = torch.from_numpy(d.astype(np.float32)).cuda()
         Ls = []
         for s in (+1.0, -1.0):
             with torch.no_grad():
                 Ls.append(focal_intensity(e.detach() + s * h * dd, plan, PlaneWave(), r0, E_init=E).item())
-            assert plan.last_forward.rel_resid <= tol
+            assert plan.last_forward.converged, plan.last_forward
     fd = (Ls[0] - Ls[1]) / (2 * h)
     assert abs(fd - slope) <= 1e-2 * abs(slope), (fd, slope, L0, h)

@@ -263,3 +263,27 @@ def test_full_size_lens_grid_warm_iterations():
     Eg = E.cpu().numpy()
     assert rel_l2(Eg, ref.E) <= 2e-5
     assert abs(st.resid0 - ref.history[0]) <= 1e-5 * ref.history[0]
+
+
+def test_warm_start_relative_to_a_cold_start():
+    """warm_start=2 measures residuals against the first residual of a start from zero: from a
+    converged field it stops after one block, with that reference as resid0; warm_start=1
+    from the same field keeps iterating against its own (tiny) first residual."""
+    torch = _torch()
+    from paper_2506_15411_gb300 import CBSError, PlaneWave
+    from paper_2506_15411_gb300._lib import CBS_ERR_ARG
+    g = co.Grid(32, 32, 32, LAM / 8, LAM, 1.0, (4, 4, 4), (4, 4, 4))
+    eps = to_dev(inputs.sphere_eps(32, 32, 32, LAM / 8, 0.8e-6, 1.4))
+    with make_plan(g, tol=1e-4, max_iter=20000, check_every=16) as plan:
+        plan.set_permittivity(eps)
+        E, st = plan.forward(PlaneWave())
+        assert st.converged and st.iters > 64
+        E2, st2 = plan.forward(PlaneWave(), E=E.clone(), warm_start=2)
+        assert st2.converged and st2.iters == 16
+        assert abs(st2.resid0 - st.resid0) <= 1e-6 * st.resid0
+        assert rel_l2(E2.cpu().numpy(), E.cpu().numpy()) <= 1e-4
+        _, st1 = plan.forward(PlaneWave(), E=E.clone(), warm_start=1)
+        assert st1.resid0 < 1e-3 * st.resid0 and st1.iters > st2.iters
+        with pytest.raises(CBSError) as e:
+            plan.forward(PlaneWave(), E=E.clone(), warm_start=3)
+        assert e.value.code == CBS_ERR_ARG
