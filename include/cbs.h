@@ -233,6 +233,71 @@ int cbs_design_step(cbs_design_t design, float* h_dev, const cbs_source* src, co
                     void* E_dev, void* Eadj_dev, float* grad_h_dev, double* objective,
                     cbs_stats* fwd, cbs_stats* adj);
 
+/* ---------------------------------------------------------------- serving
+ * A request server with continuous batching.  Submitted requests queue; a worker thread
+ * admits them into slots (a plan, its stream and field buffers for one grid shape) while
+ * the device-memory budget and max_active allow, and advances every admitted request one
+ * block of check_every iterations at a time without waiting on any one of them, so that
+ * requests arriving while others run start as soon as a slot and memory are free and their
+ * work interleaves on the GPU.  Idle slots are kept for later requests of the same shape and
+ * evicted, least recently used first, when memory is needed.  Fields stay in the slot's
+ * device memory; only the outputs a request asks for are copied out.  A request's result
+ * does not depend on what else runs: slots share no device memory and every kernel and
+ * reduction has a fixed order.  The server works on the device current at creation.  Not a
+ * part of the paper; the serving layer of this library. */
+typedef struct cbs_server_s* cbs_server_t;
+
+typedef struct {
+  double hbm_budget_bytes;  /* device bytes the slots may hold; 0 = 80 % of the free memory */
+  int max_active;           /* requests admitted at once (>= 1) */
+  double tol;               /* solver settings of every request (as in cbs_plan_desc) */
+  int max_iter;
+  int check_every;
+} cbs_server_desc;
+
+typedef struct {
+  int nx, ny, nz;           /* grid and physics as in cbs_plan_desc */
+  double pitch_m, lambda_m, n_bg;
+  int pad_lo[3], pad_hi[3];
+  const float* eps_host;    /* permittivity float32 [nz][ny][nx]: exactly one of eps_host */
+  const float* eps_dev;     /* (read with a blocking copy at admission) and eps_dev */
+  cbs_source src;           /* plane wave or point source; warm_start 0 */
+  int adjoint;              /* nonzero: also the adjoint solve of |E(r0)|^2 and the gradient */
+  int r0[3];                /* objective voxel; |E(r0)|^2 is reported for every request */
+  void* E_host;             /* optional outputs (NULL = not copied): the field, complex64 */
+  void* E_dev;              /*   [3][nz][ny][nx], to host (pinned avoids a blocking copy) or */
+  float* grad_host;         /*   device memory; the gradient dL/d eps_r, float32 [nz][ny][nx] */
+  float* grad_dev;          /*   (adjoint requests only) */
+} cbs_request;
+/* Every pointer in a request must stay valid until its result has been taken. */
+
+typedef struct {
+  long long id;             /* as returned by cbs_server_submit */
+  int status;               /* CBS_OK, the forward's or adjoint's NOT_CONVERGED / STAGNATED,
+                               or the error that ended the request */
+  double objective;         /* |E(r0)|^2 */
+  cbs_stats fwd, adj;       /* adj is zero for forward-only requests */
+  double t_submit, t_admit, t_done;   /* CLOCK_MONOTONIC seconds */
+  char error[192];          /* message when status is an error */
+} cbs_result;
+
+/* Start / stop a server (stop finishes the admitted requests; queued ones end with
+ * CBS_ERR_STATE).  Errors: CBS_ERR_ARG, CBS_ERR_CUDA. */
+int cbs_server_create(cbs_server_t* out, const cbs_server_desc* desc);
+void cbs_server_destroy(cbs_server_t server);
+
+/* Queue a request (thread-safe); *id receives its number.  Errors: CBS_ERR_ARG (bad grid,
+ * r0, source or eps pointers), CBS_ERR_STATE (closing).  Plan errors (unsupported sizes,
+ * device memory) come back in the result. */
+int cbs_server_submit(cbs_server_t server, const cbs_request* req, long long* id);
+
+/* Take up to max completed results (in completion order), waiting up to timeout_s seconds
+ * for the first; *n receives the count (0 on timeout). */
+int cbs_server_take(cbs_server_t server, cbs_result* out, int max, double timeout_s, int* n);
+
+/* Requests waiting for admission, requests admitted, device bytes held by slots. */
+int cbs_server_info(cbs_server_t server, long long* queued, long long* active, double* bytes_used);
+
 /* Free the plan and its device memory (NULL is a no-op). */
 void cbs_destroy(cbs_plan_t plan);
 

@@ -30,7 +30,8 @@ EXPORTS = ("cbs_plan", "cbs_set_permittivity", "cbs_get_splitting", "cbs_set_sol
            "cbs_forward", "cbs_adjoint", "cbs_gradient", "cbs_objective", "cbs_design_step_host",
            "cbs_set_profiling", "cbs_pass_times", "cbs_splitting_noalloc", "cbs_destroy",
            "cbs_last_error", "cbs_design_create", "cbs_design_destroy", "cbs_design_reset",
-           "cbs_design_permittivity", "cbs_design_height_gradient", "cbs_design_adam", "cbs_design_step")
+           "cbs_design_permittivity", "cbs_design_height_gradient", "cbs_design_adam", "cbs_design_step",
+           "cbs_server_create", "cbs_server_destroy", "cbs_server_submit", "cbs_server_take", "cbs_server_info")
 
 PASS_NAMES = ("k_xpass_fwd", "k_ypass_fwd", "k_zpass_green", "k_ypass_inv", "k_xpass_inv_update")
 
@@ -59,6 +60,26 @@ class cbs_design_desc(Structure):
                 ("beta2", c_double), ("adam_eps", c_double)]
 
 
+class cbs_server_desc(Structure):
+    _fields_ = [("hbm_budget_bytes", c_double), ("max_active", c_int), ("tol", c_double), ("max_iter", c_int),
+                ("check_every", c_int)]
+
+
+class cbs_request(Structure):
+    _fields_ = [("nx", c_int), ("ny", c_int), ("nz", c_int),
+                ("pitch_m", c_double), ("lambda_m", c_double), ("n_bg", c_double),
+                ("pad_lo", c_int * 3), ("pad_hi", c_int * 3),
+                ("eps_host", c_void_p), ("eps_dev", c_void_p), ("src", cbs_source), ("adjoint", c_int),
+                ("r0", c_int * 3), ("E_host", c_void_p), ("E_dev", c_void_p), ("grad_host", c_void_p),
+                ("grad_dev", c_void_p)]
+
+
+class cbs_result(Structure):
+    _fields_ = [("id", ctypes.c_longlong), ("status", c_int), ("objective", c_double),
+                ("fwd", cbs_stats), ("adj", cbs_stats), ("t_submit", c_double), ("t_admit", c_double),
+                ("t_done", c_double), ("error", ctypes.c_char * 192)]
+
+
 class CBSError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"CBS error {code}: {msg}")
@@ -85,6 +106,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "cbs_pass_times": (c_int, [P, POINTER(c_double * 5), POINTER(ctypes.c_longlong * 5), c_int]),
         "cbs_splitting_noalloc": (c_int, [POINTER(cbs_plan_desc), P, POINTER(c_double), POINTER(c_double)]),
         "cbs_destroy": (None, [P]),
+        "cbs_server_create": (c_int, [POINTER(c_void_p), POINTER(cbs_server_desc)]),
+        "cbs_server_destroy": (None, [P]),
+        "cbs_server_submit": (c_int, [P, POINTER(cbs_request), POINTER(ctypes.c_longlong)]),
+        "cbs_server_take": (c_int, [P, POINTER(cbs_result), c_int, c_double, POINTER(c_int)]),
+        "cbs_server_info": (c_int, [P, POINTER(ctypes.c_longlong), POINTER(ctypes.c_longlong), POINTER(c_double)]),
         "cbs_design_create": (c_int, [POINTER(c_void_p), P, POINTER(cbs_design_desc)]),
         "cbs_design_destroy": (None, [P]),
         "cbs_design_reset": (c_int, [P]),

@@ -158,6 +158,8 @@ bool same_source(const SourceArgs& a, const SourceArgs& b) {
 }  // namespace
 
 namespace cbs {
+// The calling thread's last error message.
+const char* last_error_message() { return g_err.c_str(); }
 // Message for cbs_last_error from other translation units.
 const char* set_last_error(const char* msg) {
   g_err = msg;

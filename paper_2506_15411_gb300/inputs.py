@@ -154,3 +154,81 @@ def random_eps(nx, ny, nz, lo=1.0, hi=2.25, seed=SEED_NOISE) -> np.ndarray:
     """Seeded uniform random permittivity, float32 (nz, ny, nx)."""
     rng = np.random.default_rng(seed)
     return rng.uniform(lo, hi, size=(nz, ny, nx)).astype(np.float32)
+
+
+# ------------------------------------------------------------------ serving request streams
+def parse_size(s: str) -> tuple:
+    """'64' -> (64, 64, 64); '192x192x128' -> (192, 192, 128)."""
+    parts = [int(v) for v in str(s).lower().split("x")]
+    return tuple(parts * 3) if len(parts) == 1 else tuple(parts)
+
+
+SERVING_SIZES = ((64, 64, 64), (128, 128, 128), (192, 192, 128), (256, 256, 192), (384, 384, 256))
+SEED_STREAM = 42
+
+
+def serving_stream(n: int, sizes=SERVING_SIZES, seed: int = SEED_STREAM, ppl: int = 8, lam: float = 1.064e-6,
+                   p_adjoint: float = 0.5, rate_hz: float | None = None) -> list:
+    """Seeded request mix: grid uniform over `sizes` at pitch lam / ppl with one-wavelength
+    absorbing layers on every face, a sphere or a Fresnel lens (equal odds) of index
+    U[1.3, 1.6], an x-polarised plane wave, forward only or forward + adjoint (p_adjoint).
+    Each request is a dict; arrivals (Poisson, rate_hz) are added when rate_hz is given."""
+    rng = np.random.default_rng(seed)
+    pitch = lam / ppl
+    out = []
+    for i in range(n):
+        nx, ny, nz = sizes[int(rng.integers(len(sizes)))]
+        kind = "sphere" if rng.random() < 0.5 else "lens"
+        n_idx = float(rng.uniform(1.3, 1.6))
+        adj = bool(rng.random() < p_adjoint)
+        pads = (ppl, ppl, ppl)
+        rq = {"index": i, "nx": nx, "ny": ny, "nz": nz, "pitch": pitch, "lam": lam, "pads": pads,
+              "structure": kind, "n": n_idx, "adjoint": adj, "pol": (1.0, 0.0, 0.0)}
+        rq["r0"] = request_focus(rq)
+        out.append(rq)
+    if rate_hz:
+        assign_arrivals(out, rate_hz, seed)
+    return out
+
+
+def assign_arrivals(reqs: list, rate_hz: float, seed: int = SEED_STREAM):
+    """Poisson arrivals: exponential gaps of mean 1 / rate_hz (seed + 1), starting at 0."""
+    rng = np.random.default_rng(seed + 1)
+    t = 0.0
+    for k, rq in enumerate(reqs):
+        if k:
+            t += float(rng.exponential(1.0 / rate_hz))
+        rq["arrival_s"] = t
+
+
+def _sphere_radius(rq) -> float:
+    inner = min(rq["nx"], rq["ny"], rq["nz"]) - 2 * max(rq["pads"])
+    return 0.3 * inner * rq["pitch"]
+
+
+def _lens_diameter(rq) -> float:
+    return 0.7 * (min(rq["nx"], rq["ny"]) - 2 * max(rq["pads"][:2])) * rq["pitch"]
+
+
+def request_focus(rq) -> tuple:
+    """Objective voxel: behind the sphere's far side, or at the lens focus (clipped into the
+    interior)."""
+    nx, ny, nz, p = rq["nx"], rq["ny"], rq["nz"], rq["pitch"]
+    z_hi = nz - rq["pads"][2] - 1
+    if rq["structure"] == "sphere":
+        z = int(round((nz - 1) / 2 + _sphere_radius(rq) / p)) + 2
+    else:
+        z = rq["pads"][2] + 2 + int(round(focal_length(_lens_diameter(rq), 0.84) / p))
+    return (nx // 2, ny // 2, min(z, z_hi))
+
+
+def request_eps(rq) -> np.ndarray:
+    """Permittivity of a request from serving_stream (float32 (nz, ny, nx))."""
+    nx, ny, nz, p = rq["nx"], rq["ny"], rq["nz"], rq["pitch"]
+    if rq["structure"] == "sphere":
+        return sphere_eps(nx, ny, nz, p, _sphere_radius(rq), rq["n"])
+    x = centred_coords(nx, p)
+    y = centred_coords(ny, p)
+    r = np.sqrt(x[None, :] ** 2 + y[:, None] ** 2)
+    h = fresnel_height(r, rq["lam"], _lens_diameter(rq), 0.84, rq["n"])
+    return height_to_eps(h, nz, p, rq["pads"][2] + 2, rq["n"])

@@ -45,6 +45,9 @@ int main(void) {
   printf("cbs_source size %zu\n", sizeof(cbs_source));
   printf("cbs_stats size %zu\n", sizeof(cbs_stats));
   printf("cbs_design_desc size %zu\n", sizeof(cbs_design_desc));
+  printf("cbs_server_desc size %zu\n", sizeof(cbs_server_desc));
+  printf("cbs_request size %zu\n", sizeof(cbs_request));
+  printf("cbs_result size %zu\n", sizeof(cbs_result));
   F(cbs_plan_desc, pitch_m); F(cbs_plan_desc, pad_lo); F(cbs_plan_desc, pad_hi); F(cbs_plan_desc, tol);
   F(cbs_plan_desc, max_iter); F(cbs_plan_desc, check_every); F(cbs_plan_desc, cuda_stream);
   F(cbs_source, pol); F(cbs_source, z_plane); F(cbs_source, r0); F(cbs_source, user_src_dev);
@@ -53,6 +56,13 @@ int main(void) {
   F(cbs_design_desc, n_lens); F(cbs_design_desc, aperture_um); F(cbs_design_desc, h_max_um);
   F(cbs_design_desc, sigma_um); F(cbs_design_desc, mirror); F(cbs_design_desc, alpha);
   F(cbs_design_desc, beta1); F(cbs_design_desc, beta2); F(cbs_design_desc, adam_eps);
+  F(cbs_server_desc, max_active); F(cbs_server_desc, tol); F(cbs_server_desc, max_iter);
+  F(cbs_server_desc, check_every);
+  F(cbs_request, pitch_m); F(cbs_request, pad_lo); F(cbs_request, eps_host); F(cbs_request, eps_dev);
+  F(cbs_request, src); F(cbs_request, adjoint); F(cbs_request, r0); F(cbs_request, E_host);
+  F(cbs_request, E_dev); F(cbs_request, grad_host); F(cbs_request, grad_dev);
+  F(cbs_result, status); F(cbs_result, objective); F(cbs_result, fwd); F(cbs_result, adj);
+  F(cbs_result, t_submit); F(cbs_result, t_admit); F(cbs_result, t_done); F(cbs_result, error);
   return 0;
 }
 ''')
@@ -65,7 +75,8 @@ int main(void) {
             t, m, v = ln.split()
             got[(t, m)] = int(v)
     types = {"cbs_plan_desc": L.cbs_plan_desc, "cbs_source": L.cbs_source, "cbs_stats": L.cbs_stats,
-             "cbs_design_desc": L.cbs_design_desc}
+             "cbs_design_desc": L.cbs_design_desc, "cbs_server_desc": L.cbs_server_desc,
+             "cbs_request": L.cbs_request, "cbs_result": L.cbs_result}
     for (t, m), v in got.items():
         if m == "size":
             assert ctypes.sizeof(types[t]) == v, (t, v)

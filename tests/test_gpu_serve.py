@@ -1,0 +1,134 @@
+"""GPU: the continuous-batching server (cbs_server_*).
+
+* every result is bit-for-bit the same alone (one request on the GPU at a time) and in a mix
+  of requests of different shapes admitted together;
+* a served solve equals the same solve through a plan (itself checked against the oracle);
+* admission never holds more device memory than the budget, and a request that can never
+  fit ends with CBS_ERR_OOM instead of waiting;
+* requests are admitted while others run (no more than max_active at a time) and their work
+  overlaps.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from paper_2506_15411_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+SIZES = ((32, 32, 32), (48, 40, 36), (64, 64, 64))
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("CUDA is not available: GPU tests need a GPU")
+    return torch
+
+
+def _stream(n, seed=5):
+    from paper_2506_15411_gb300.serve import stream_request
+    return [stream_request(rq) for rq in inputs.serving_stream(n, SIZES, seed=seed, ppl=8)]
+
+
+def _submit(srv, rq):
+    return srv.submit(rq["grid"], inputs.request_eps(rq), rq["source"], rq["r0"], adjoint=rq["adjoint"],
+                      want_field=True, want_grad=rq["adjoint"], tag=rq["index"])
+
+
+def test_results_are_identical_alone_and_in_the_mix():
+    torch = _torch()
+    from paper_2506_15411_gb300.serve import Server
+    reqs = _stream(8)
+    assert len({rq["grid"] for rq in reqs}) >= 2 and any(rq["adjoint"] for rq in reqs)
+    alone = {}
+    with Server(max_active=1, tol=1e-4, check_every=16) as srv:
+        for rq in reqs:
+            _submit(srv, rq)
+            r = srv.wait(1)[0]
+            alone[r.tag] = r
+    with Server(max_active=8, tol=1e-4, check_every=16) as srv:
+        for rq in reqs:
+            _submit(srv, rq)
+        mix = {r.tag: r for r in srv.wait(len(reqs))}
+    torch.cuda.synchronize()
+    for rq in reqs:
+        a, b = alone[rq["index"]], mix[rq["index"]]
+        assert a.ok and b.ok, (a.error, b.error)
+        assert a.fwd.iters == b.fwd.iters and a.adj.iters == b.adj.iters
+        assert a.objective == b.objective
+        assert torch.equal(a.E, b.E)
+        if rq["adjoint"]:
+            assert a.adj.iters > 0 and torch.equal(a.grad, b.grad)
+
+
+def test_served_solve_equals_the_plan_path():
+    torch = _torch()
+    from paper_2506_15411_gb300 import CBSPlan
+    from paper_2506_15411_gb300.serve import Server
+    rq = [q for q in _stream(8) if q["adjoint"]][0]
+    g = rq["grid"]
+    eps = inputs.request_eps(rq)
+    with Server(max_active=2, tol=1e-4, check_every=16) as srv:
+        _submit(srv, rq)
+        r = srv.wait(1)[0]
+    with CBSPlan(g.nx, g.ny, g.nz, g.pitch, g.lam, g.n_bg, g.pad_lo, g.pad_hi, tol=1e-4, check_every=16) as plan:
+        plan.set_permittivity(torch.from_numpy(eps).cuda())
+        E, st = plan.forward(rq["source"])
+        Ea, sa = plan.adjoint(rq["r0"], E)
+        grad, obj = plan.gradient(E, Ea, rq["r0"])
+        torch.cuda.synchronize()
+    assert r.ok and st.converged and sa.converged
+    assert r.fwd.iters == st.iters and r.adj.iters == sa.iters
+    assert r.objective == obj
+    assert torch.equal(r.E, E) and torch.equal(r.grad, grad)
+
+
+def test_admission_stays_within_the_memory_budget():
+    torch = _torch()
+    from paper_2506_15411_gb300._lib import CBS_ERR_OOM
+    from paper_2506_15411_gb300.serve import Server
+    reqs = _stream(10, seed=9)
+    big = max(rq["grid"].nx * rq["grid"].ny * rq["grid"].nz for rq in reqs)
+    budget = 2.0 * big * 140 / 1e9 + 0.04     # room for about two of the largest slots
+    with Server(max_active=8, hbm_budget_gb=budget, tol=1e-3, check_every=16) as srv:
+        for rq in reqs:
+            _submit(srv, rq)
+        peak = 0.0
+        got = []
+        while len(got) < len(reqs):
+            got += srv.take(64, 0.01)
+            peak = max(peak, srv.info()["bytes_used"])
+        assert all(r.ok for r in got)
+        assert 0 < peak <= budget * 1e9
+        # a grid whose slot alone is over the budget fails instead of waiting
+        huge = dict(reqs[0], grid=type(reqs[0]["grid"])(256, 256, 256, reqs[0]["grid"].pitch, reqs[0]["grid"].lam,
+                                                          1.0, (8, 8, 8), (8, 8, 8)))
+        srv.submit(huge["grid"], np.ones((256, 256, 256), np.float32), huge["source"], (128, 128, 128))
+        r = srv.wait(1)[0]
+        assert r.status == CBS_ERR_OOM and "budget" in r.error
+    torch.cuda.synchronize()
+
+
+def test_requests_are_admitted_while_others_run():
+    torch = _torch()
+    from paper_2506_15411_gb300.serve import Server
+    reqs = [q for q in _stream(24, seed=11) if q["grid"].nx == 64][:6]
+    assert len(reqs) == 6
+    with Server(max_active=3, tol=1e-4, check_every=16) as srv:
+        for rq in reqs:
+            srv.submit(rq["grid"], inputs.request_eps(rq), rq["source"], rq["r0"], adjoint=rq["adjoint"])
+        res = srv.wait(len(reqs))
+    torch.cuda.synchronize()
+    assert all(r.ok for r in res)
+    # never more than max_active admitted at once
+    for r in res:
+        running = sum(1 for q in res if q.t_admit <= r.t_admit < q.t_done)
+        assert running <= 3
+    # the first three run together; the others start as slots free up, before all are done
+    first = sorted(res, key=lambda r: r.t_admit)
+    assert first[1].t_admit < first[0].t_done and first[2].t_admit < first[0].t_done
+    later = first[3:]
+    assert all(r.t_admit >= min(q.t_done for q in first[:3]) - 1e-3 for r in later)
+    assert min(r.t_admit for r in later) < max(q.t_done for q in first[:3])

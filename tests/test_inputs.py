@@ -70,3 +70,22 @@ def test_seeded_generators_are_reproducible():
     e2, _ = inputs.design_slab_eps(64, 64, 48, LAM / 8, LAM, slab=(32, 32, 8), z_base=10)
     assert np.array_equal(e1, e2)
     assert e1[reg].min() >= 1.0 and e1[reg].max() <= 2.25 + 1e-6
+
+
+def test_serving_stream_is_seeded_and_poisson():
+    a = inputs.serving_stream(500, seed=42, rate_hz=4.0)
+    b = inputs.serving_stream(500, seed=42, rate_hz=4.0)
+    assert [(q["nx"], q["structure"], q["n"], q["adjoint"], q["arrival_s"]) for q in a] == \
+           [(q["nx"], q["structure"], q["n"], q["adjoint"], q["arrival_s"]) for q in b]
+    gaps = np.diff([q["arrival_s"] for q in a])
+    assert abs(gaps.mean() - 0.25) < 0.03 and abs(gaps.std() - 0.25) < 0.04     # exponential: mean = std
+    assert {q["structure"] for q in a} == {"sphere", "lens"}
+    assert all(1.3 <= q["n"] <= 1.6 for q in a)
+    assert 0.4 < np.mean([q["adjoint"] for q in a]) < 0.6
+    assert {(q["nx"], q["ny"], q["nz"]) for q in a} == set(inputs.SERVING_SIZES)
+    for q in a[:40]:
+        x, y, z = q["r0"]
+        assert q["pads"][2] <= z < q["nz"] - q["pads"][2] and x == q["nx"] // 2 and y == q["ny"] // 2
+    small = inputs.serving_stream(4, sizes=((32, 32, 32),), seed=1)
+    e = inputs.request_eps(small[0])
+    assert e.shape == (32, 32, 32) and e.dtype == np.float32 and 1.0 <= e.min() and e.max() <= 1.6 ** 2 + 1e-6
