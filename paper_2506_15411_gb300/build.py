@@ -40,15 +40,19 @@ def _headers_mtime() -> float:
     return max(os.path.getmtime(h) for h in hs)
 
 
-def build(verbose: bool = False, extra_flags=()) -> str:
-    """Compile (if stale) and link; returns the library path."""
-    os.makedirs(OBJDIR, exist_ok=True)
+def build(verbose: bool = False, extra_flags=(), libdir: str = LIBDIR) -> str:
+    """Compile (if stale) and link into libdir/libcbs.so; returns the library path.
+    extra_flags (e.g. -D settings of the launch heuristics) are for builds kept apart in
+    their own libdir."""
+    objdir = os.path.join(libdir, "_build")
+    lib = os.path.join(libdir, "libcbs.so")
+    os.makedirs(objdir, exist_ok=True)
     cc = nvcc()
     hdr = _headers_mtime()
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(OBJDIR, src.replace(".cu", ".o"))
+        o = os.path.join(objdir, src.replace(".cu", ".o"))
         if not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), hdr):
             jobs.append([cc, *ARCH, *FLAGS, *extra_flags, "-c", s, "-o", o])
 
@@ -63,12 +67,12 @@ def build(verbose: bool = False, extra_flags=()) -> str:
 
     with ThreadPoolExecutor(max_workers=max(1, len(jobs))) as ex:
         list(ex.map(run, jobs))
-    objs = [os.path.join(OBJDIR, s.replace(".cu", ".o")) for s in SOURCES]
-    if jobs or not os.path.exists(LIB):
-        tmp = LIB + ".tmp"
+    objs = [os.path.join(objdir, s.replace(".cu", ".o")) for s in SOURCES]
+    if jobs or not os.path.exists(lib):
+        tmp = lib + ".tmp"
         run([cc, *ARCH, "-shared", "-o", tmp, *objs])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -41,6 +41,14 @@ namespace {
 thread_local std::string g_err;
 
 constexpr double kPiD = 3.14159265358979323846;
+#ifndef CBS_MAX_YZ_OCC
+#define CBS_MAX_YZ_OCC 2
+#endif
+#ifndef CBS_MIN_OCC2_TX
+#define CBS_MIN_OCC2_TX 8
+#endif
+constexpr int kMaxYZOcc = CBS_MAX_YZ_OCC;    // a build with 1 keeps every y/z kernel at one block per SM
+constexpr int kMinOcc2Tx = CBS_MIN_OCC2_TX;  // narrowest tile worth two blocks per SM
 constexpr int kMaxN = 1024;
 
 // Factor n into the supported radices (at most max_radix): fewest stages first, then the
@@ -332,7 +340,6 @@ bool series_absorb_block(cbs_plan_s* p, SeriesRun& R) {
   }
   R.rc = collect_pass_times(p);
   if (R.rc) return true;
-  bool done = false;
   for (int k = 0; k < R.m; ++k) {
     ++R.it;
     const double r = std::sqrt(p->hist_host[k]);
@@ -342,14 +349,14 @@ bool series_absorb_block(cbs_plan_s* p, SeriesRun& R) {
       R.rc = fail(CBS_ERR_DIVERGED, "series diverged at iteration %d (relative residual %g)", R.it, R.rel);
       return true;
     }
-    // a converged iteration inside a block still lets the block finish: `it` counts every
-    // iteration that ran and `rel` is the residual of the last one
-    if (p->d.tol > 0 && R.rel <= p->d.tol) done = true;
     if (R.rel < 0.99 * R.best) {
       R.best = R.rel;
       R.best_it = R.it;
     }
   }
+  // converged when the residual at the check (the block's last iteration) is within tol; a
+  // dip below tol earlier in the block does not count (the residual is not monotone)
+  const bool done = p->d.tol > 0 && R.rel <= p->d.tol;
   // stagnation: the residual has sat at its rounding floor for a long stretch
   if (!done && p->d.tol > 0 && R.it - R.best_it >= std::max(1000, R.it / 4)) {
     R.rc = fail(CBS_ERR_STAGNATED, "residual stagnated at %g (best %g) after %d iterations, above tol %g", R.rel,
@@ -583,7 +590,7 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
   // launch shapes: persistent, double-buffered tile kernels, one block per SM (about 220 KB
   // of shared memory each): x tiles of rpb rows, y and z tiles of TX columns by whole
   // tensor-copy boxes, TX as wide as fits
-  const size_t kBlockBudget = 220 * 1024;
+  const size_t kBlockBudget = 220 * 1024, kBlockBudget2 = 110 * 1024;
   a.nxp = round_up(d.nx, 16);
   a.Nw = (size_t)a.nxp * d.ny * d.nz;
   {
@@ -591,28 +598,50 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
     const size_t fixed = (size_t)round_up(d.nx * (int)sizeof(float2), 16) + 24 + 32 * 8;
     a.rpb = (int)std::max<size_t>(1, std::min<size_t>(64, (kBlockBudget - fixed) / per_row));
   }
-  a.yb = std::min(kBoxRows, round_up(d.ny, 4));
-  a.zb = std::min(kBoxRows, round_up(d.nz, 4));
-  a.nyr = round_up(d.ny, a.yb);
-  a.nzr = round_up(d.nz, a.zb);
+  // y and z tiles: TX columns x whole axis, brought in by boxes of B rows.  B is a divisor of
+  // the axis in [16, 64] when one keeps every box's shared-memory offset (B TX 8 bytes) a
+  // multiple of 128 bytes -- then no padded rows are held -- else 64 (rows past the axis
+  // read as zero and are not stored); a short axis is one box.
+  auto box_rows = [](int n, int tx) {
+    if (n <= kBoxRows) return round_up(n, 4);
+    for (int b = kBoxRows; b >= 16; --b)
+      if (n % b == 0 && (b * tx) % 16 == 0) return b;
+    return kBoxRows;
+  };
   const size_t twy_b = round_up(d.ny * (int)sizeof(float2), 16), twz_b = round_up(d.nz * (int)sizeof(float2), 16);
-  auto ysmem = [&](int tx, int nb) { return (size_t)(nb * a.nyr + d.ny) * tx * sizeof(float2) + twy_b + 8 * nb + 8; };
-  auto zsmem = [&](int tx, int nb) { return (size_t)3 * (nb + 1) * a.nzr * tx * sizeof(float2) + twz_b + 8 * nb + 8; };
-  // widest tile with three buffers, else with two
-  bool fits = false;
-  for (int nb = 3; nb >= 2 && !fits; --nb)
-    for (int tx = 16; tx >= 8 && !fits; tx /= 2)
-      if (ysmem(tx, nb) <= kBlockBudget) { a.tx_y = tx; a.nbuf_y = nb; fits = true; }
-  if (!fits) { a.tx_y = 4; a.nbuf_y = 2; }
-  fits = false;
-  for (int nb = 3; nb >= 2 && !fits; --nb)
-    for (int tx = 16; tx >= 8 && !fits; tx /= 2)
-      if (zsmem(tx, nb) <= kBlockBudget) { a.tx_z = tx; a.nbuf_z = nb; fits = true; }
-  if (!fits) { a.tx_z = 4; a.nbuf_z = 2; }
-  if (ysmem(a.tx_y, a.nbuf_y) > kBlockBudget || zsmem(a.tx_z, a.nbuf_z) > kBlockBudget) {
+  auto ysmem = [&](int tx, int nb) {
+    const int rows = round_up(d.ny, box_rows(d.ny, tx));
+    return (size_t)(nb * rows + d.ny) * tx * sizeof(float2) + twy_b + 8 * nb + 8;
+  };
+  auto zsmem = [&](int tx, int nb) {
+    return (size_t)3 * (nb + 1) * round_up(d.nz, box_rows(d.nz, tx)) * tx * sizeof(float2) + twz_b + 8 * nb + 8;
+  };
+  auto max_radix = [](const AxisPlan& ap) {
+    int m = 1;
+    for (int i = 0; i < ap.ns; ++i) m = std::max(m, ap.r[i]);
+    return m;
+  };
+  // Two blocks per SM (half the shared memory each) when the axis needs no radix above 11,
+  // else one: the widest tile, then the most buffers, that fits.
+  auto pick = [&](auto smem, int maxr, int& tx, int& nb, int& occ) {
+    for (occ = (maxr <= 11 && kMaxYZOcc >= 2) ? 2 : 1; occ >= 1; --occ) {
+      const size_t budget = occ == 2 ? kBlockBudget2 : kBlockBudget;
+      for (tx = 16; tx >= (occ == 2 ? kMinOcc2Tx : 4); tx /= 2)
+        for (nb = 3; nb >= 2; --nb)
+          if (smem(tx, nb) <= budget) return true;
+    }
+    return false;
+  };
+  const bool fy = pick(ysmem, max_radix(ay), a.tx_y, a.nbuf_y, a.occ_y);
+  const bool fz = pick(zsmem, max_radix(az), a.tx_z, a.nbuf_z, a.occ_z);
+  if (!fy || !fz) {
     fail(CBS_ERR_ARG, "axis too long for the shared-memory tiles");
     return bail(CBS_ERR_ARG);
   }
+  a.yb = box_rows(d.ny, a.tx_y);
+  a.zb = box_rows(d.nz, a.tx_z);
+  a.nyr = round_up(d.ny, a.yb);
+  a.nzr = round_up(d.nz, a.zb);
 
   const size_t N = p->N;
   CKP(cudaMalloc(&p->V, a.Nw * sizeof(float2)));

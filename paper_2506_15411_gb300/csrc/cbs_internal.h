@@ -65,6 +65,7 @@ struct IterArgs {
   int rpb;                // rows per tile, x passes
   int tx_y, tx_z;         // x-columns per tile, y and z passes
   int nbuf_y, nbuf_z;     // tile buffers of the pipelined y and z passes (2 or 3)
+  int occ_y, occ_z;       // blocks per SM of the y and z kernels (2: radices <= 11, 64 registers)
   int grid_x, grid_xf, grid_y, grid_z;   // persistent grid sizes (x inverse, x forward, y, z)
 };
 

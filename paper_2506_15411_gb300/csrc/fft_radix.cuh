@@ -190,7 +190,9 @@ template <bool INV> struct DFT<12, INV> : DFTSplit<3, 4, INV> {};
 template <bool INV> struct DFT<16, INV> : DFTSplit<4, 4, INV> {};
 
 // Calls f(std::integral_constant<int, R>) for the runtime radix r (uniform across the block).
-template <class F>
+// Radices above MAXR are not compiled in (a plan whose axes need them uses a MAXR = 16
+// kernel); leaving them out keeps the register allocation to what the smaller radices need.
+template <int MAXR = 16, class F>
 __device__ __forceinline__ void radix_dispatch(int r, F&& f) {
   switch (r) {
     case 1: f(std::integral_constant<int, 1>{}); break;
@@ -201,12 +203,12 @@ __device__ __forceinline__ void radix_dispatch(int r, F&& f) {
     case 6: f(std::integral_constant<int, 6>{}); break;
     case 7: f(std::integral_constant<int, 7>{}); break;
     case 8: f(std::integral_constant<int, 8>{}); break;
-    case 9: f(std::integral_constant<int, 9>{}); break;
-    case 10: f(std::integral_constant<int, 10>{}); break;
-    case 11: f(std::integral_constant<int, 11>{}); break;
-    case 12: f(std::integral_constant<int, 12>{}); break;
-    case 13: f(std::integral_constant<int, 13>{}); break;
-    case 16: f(std::integral_constant<int, 16>{}); break;
+    case 9: if constexpr (MAXR >= 9) f(std::integral_constant<int, 9>{}); break;
+    case 10: if constexpr (MAXR >= 10) f(std::integral_constant<int, 10>{}); break;
+    case 11: if constexpr (MAXR >= 11) f(std::integral_constant<int, 11>{}); break;
+    case 12: if constexpr (MAXR >= 12) f(std::integral_constant<int, 12>{}); break;
+    case 13: if constexpr (MAXR >= 13) f(std::integral_constant<int, 13>{}); break;
+    case 16: if constexpr (MAXR >= 16) f(std::integral_constant<int, 16>{}); break;
     default: break;
   }
 }

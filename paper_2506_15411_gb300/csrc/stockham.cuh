@@ -154,7 +154,7 @@ __device__ __forceinline__ void stage_cols2(const float2* src, float2* dst, int 
 // the transform writes A (its outputs sit where it read them, so that is safe from either
 // buffer).  Returns the buffer holding the output of stage q1 - 1.  Barrier after each stage;
 // `after_first` runs after the first of them.
-template <bool INV, int NCOL, class Hook = NoHook>
+template <bool INV, int NCOL, int MAXR = 16, class Hook = NoHook>
 __device__ __forceinline__ float2* cols2_stages(float2* in, float2* A, float2* B, int ncomp, int cs,
                                                 const AxisPlan& ap, int q0, int q1, const float2* tw, int tid,
                                                 int nth, Hook after_first = Hook{}) {
@@ -163,7 +163,7 @@ __device__ __forceinline__ float2* cols2_stages(float2* in, float2* A, float2* B
     const int4 g = stage_of(ap, q);
     const float2 iv = stage_inv(ap, q);
     float2* out = (q == ap.ns - 1) ? A : (src == A ? B : A);
-    radix_dispatch(g.x, [&](auto Ri) {
+    radix_dispatch<MAXR>(g.x, [&](auto Ri) {
       constexpr int R = decltype(Ri)::value;
       stage_cols2<R, INV, NCOL>(src, out, ncomp, cs, g, iv, tw, tid, nth);
     });
@@ -215,7 +215,7 @@ __device__ __forceinline__ void stage_rows(const float2* src, float2* dst, bool 
 // holding the (unswizzled) result: A, or B when the last of several stages reads A (its
 // swizzled reads and unswizzled writes must not share a buffer).  `after_first` as for
 // fft_cols.  Ends with a barrier.
-template <bool INV, class Hook = NoHook>
+template <bool INV, int MAXR = 16, class Hook = NoHook>
 __device__ __forceinline__ float2* fft_rows(float2* A, float2* B, int nrows, int ncomp, int ld, int cs,
                                             const AxisPlan& ap, const float2* tw, int tid, int nth,
                                             Hook after_first = Hook{}) {
@@ -228,7 +228,7 @@ __device__ __forceinline__ float2* fft_rows(float2* A, float2* B, int nrows, int
     const float2 iv = stage_inv(ap, q);
     const bool last = (q == ns - 1);
     out = !last ? dst : (q > 0 ? dst : A);
-    radix_dispatch(g.x, [&](auto Ri) {
+    radix_dispatch<MAXR>(g.x, [&](auto Ri) {
       constexpr int R = decltype(Ri)::value;
       stage_rows<R, INV>(src, out, q > 0, !last, nrows, ncomp, ld, cs, g, iv, tw, tid, nth);
     });

@@ -33,11 +33,11 @@ __device__ __forceinline__ void green(float px, float py, float pz, float qx, fl
   const float p2 = px * px + py * py + pz * pz;
   const float nyq2 = (px * px - qx * qx) + (py * py - qy * qy) + (pz * pz - qz * qz);
   const float cr = nyq2 - kt2.x, ci = -kt2.y;
-  const float cs = 1.f / (cr * cr + ci * ci);
+  const float cs = __frcp_rn(cr * cr + ci * ci);
   const float2 qd = make_float2(qx * X0.x + qy * X1.x + qz * X2.x, qx * X0.y + qy * X1.y + qz * X2.y);
   const float2 c = cmul(qd, make_float2(cr * cs, -ci * cs));
   const float dr = p2 - kt2.x, di = -kt2.y;
-  const float sc = invN / (dr * dr + di * di);
+  const float sc = invN * __frcp_rn(dr * dr + di * di);
   const float2 inv = make_float2(dr * sc, -di * sc);   // invN / (dr + i di)
   X0 = cmul(make_float2(X0.x + qx * c.x, X0.y + qx * c.y), inv);
   X1 = cmul(make_float2(X1.x + qy * c.x, X1.y + qy * c.y), inv);
@@ -52,8 +52,12 @@ constexpr int kYZThreads = 512;
 // of the tile that last used that buffer has been read out; with 3 buffers that store was
 // issued a whole tile earlier), and the store of tile i drains meanwhile.  Twiddles are
 // loaded once.
-template <int TX, bool INV>
-__global__ void __launch_bounds__(kYZThreads, 1) k_ypass(const __grid_constant__ CUtensorMap tm, const IterArgs a) {
+// OCC blocks per SM: 1 (up to 128 registers, all radices) or 2 (64 registers, radices up to
+// MAXR = 11, half the shared memory each; two independent blocks keep issuing while the
+// other waits at a barrier).
+template <int TX, bool INV, int OCC>
+__global__ void __launch_bounds__(kYZThreads, OCC) k_ypass(const __grid_constant__ CUtensorMap tm, const IterArgs a) {
+  constexpr int MAXR = OCC == 1 ? 16 : 11;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int tileN = a.nyr * TX, nbuf = a.nbuf_y;
   float2* buf0 = reinterpret_cast<float2*>(smem_raw);   // nbuf x [nyr][TX]
@@ -94,7 +98,7 @@ __global__ void __launch_bounds__(kYZThreads, 1) k_ypass(const __grid_constant__
         issue(tn, nxb, nbar);
       }
     };
-    cols2_stages<INV, TX>(cur, cur, scr, 1, 0, a.ay, 0, a.ay.ns, tw, tid, nth, prefetch);
+    cols2_stages<INV, TX, MAXR>(cur, cur, scr, 1, 0, a.ay, 0, a.ay.ns, tw, tid, nth, prefetch);
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {
@@ -151,12 +155,37 @@ __device__ __forceinline__ void stage_last_green(const float2* src, float2* A, i
   }
 }
 
-// Persistent, multi-buffered z pass (same pipeline as the y pass): FFT_z of the three
-// components of a tile (their stages run together), the k-space multiply fused into the last
-// forward stage, IFFT_z.
+// The k-space multiply as its own sweep over a transformed tile (one thread per (z, column)
+// point, all three components): the two-blocks-per-SM variant has no registers for the fused
+// last stage.
 template <int TX>
-__global__ void __launch_bounds__(kYZThreads, 1) k_zpass_green(const __grid_constant__ CUtensorMap tm,
-                                                               const IterArgs a) {
+__device__ __forceinline__ void green_sweep(float2* A, int cs, int x0, float py, float qy, int tid, int nth,
+                                            const IterArgs& a) {
+  const float two_pi = 6.283185307179586f;
+  const float kx = two_pi / (float)a.nx, kz = two_pi / (float)a.nz;
+  for (int k = tid; k < TX * a.nz; k += nth) {
+    const int col = k % TX, iz = k / TX;
+    const int x = x0 + col;
+    const float px = kx * (float)fft_freq(x, a.nx);
+    const float qx = (2 * x == a.nx) ? 0.f : px;
+    const float pz = kz * (float)fft_freq(iz, a.nz);
+    const float qz = (2 * iz == a.nz) ? 0.f : pz;
+    const int o = iz * TX + col;
+    float2 v0 = A[o], v1 = A[cs + o], v2 = A[2 * cs + o];
+    green(px, py, pz, qx, qy, qz, a.kt2, a.invN, v0, v1, v2);
+    A[o] = v0;
+    A[cs + o] = v1;
+    A[2 * cs + o] = v2;
+  }
+}
+
+// Persistent, multi-buffered z pass (same pipeline as the y pass): FFT_z of the three
+// components of a tile (their stages run together), the k-space multiply (fused into the last
+// forward stage when OCC = 1, a separate sweep when OCC = 2), IFFT_z.
+template <int TX, int OCC>
+__global__ void __launch_bounds__(kYZThreads, OCC) k_zpass_green(const __grid_constant__ CUtensorMap tm,
+                                                                 const IterArgs a) {
+  constexpr int MAXR = OCC == 1 ? 16 : 11;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int nzr = a.nzr;
   const int cs = nzr * TX, tileN = 3 * cs, nbuf = a.nbuf_z;
@@ -204,17 +233,21 @@ __global__ void __launch_bounds__(kYZThreads, 1) k_zpass_green(const __grid_cons
     const int x0 = xt * TX;
     const float py = two_pi / (float)a.ny * (float)fft_freq(y, a.ny);
     const float qy = (2 * y == a.ny) ? 0.f : py;
-    float2* P = cols2_stages<false, TX>(cur, cur, scr, 3, cs, a.az, 0, ns - 1, tw, tid, nth, prefetch);
-    {
+    if constexpr (OCC == 1) {
+      float2* P = cols2_stages<false, TX, MAXR>(cur, cur, scr, 3, cs, a.az, 0, ns - 1, tw, tid, nth, prefetch);
       const int4 g = stage_of(a.az, ns - 1);
-      radix_dispatch(g.x, [&](auto Ri) {
+      radix_dispatch<MAXR>(g.x, [&](auto Ri) {
         constexpr int R = decltype(Ri)::value;
         stage_last_green<R, TX>(P, cur, cs, g, tw, tid, nth, x0, py, qy, a);
       });
+      __syncthreads();
+      if (ns == 1) prefetch();
+    } else {
+      cols2_stages<false, TX, MAXR>(cur, cur, scr, 3, cs, a.az, 0, ns, tw, tid, nth, prefetch);
+      green_sweep<TX>(cur, cs, x0, py, qy, tid, nth, a);
+      __syncthreads();
     }
-    __syncthreads();
-    if (ns == 1) prefetch();
-    cols2_stages<true, TX>(cur, cur, scr, 3, cs, a.az, 0, ns, tw, tid, nth);
+    cols2_stages<true, TX, MAXR>(cur, cur, scr, 3, cs, a.az, 0, ns, tw, tid, nth);
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {
@@ -248,41 +281,56 @@ size_t zpass_smem(const IterArgs& a) {
 int ypass_tiles(const IterArgs& a) { return (a.nx + a.tx_y - 1) / a.tx_y * a.nz * 3; }
 int zpass_tiles(const IterArgs& a) { return (a.nx + a.tx_z - 1) / a.tx_z * a.ny; }
 
+template <class F>
+cudaError_t with_occ(int occ, F&& f) {
+  return occ == 2 ? f(std::integral_constant<int, 2>{}) : f(std::integral_constant<int, 1>{});
+}
+
 // Persistent grids: as many blocks as fit on the device at once (capped by the tile count).
 cudaError_t yz_grid_sizes(IterArgs& a, int sms) {
-  return with_tx(a.tx_y, [&](auto T) {
-    constexpr int TX = decltype(T)::value;
-    int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ypass<TX, false>, kYZThreads, ypass_smem(a));
-    if (e != cudaSuccess) return e;
-    a.grid_y = std::max(1, std::min(ypass_tiles(a), sms * std::max(1, occ)));
-    return with_tx(a.tx_z, [&](auto T2) {
-      constexpr int TZ = decltype(T2)::value;
-      int occz = 0;
-      cudaError_t e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occz, k_zpass_green<TZ>, kYZThreads, zpass_smem(a));
-      if (e2 != cudaSuccess) return e2;
-      a.grid_z = std::max(1, std::min(zpass_tiles(a), sms * std::max(1, occz)));
-      return cudaSuccess;
+  cudaError_t e = with_tx(a.tx_y, [&](auto T) {
+    return with_occ(a.occ_y, [&](auto O) {
+      constexpr int TX = decltype(T)::value, OCC = decltype(O)::value;
+      int occ = 0;
+      cudaError_t e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ypass<TX, false, OCC>, kYZThreads,
+                                                                     ypass_smem(a));
+      if (e1 == cudaSuccess) a.grid_y = std::max(1, std::min(ypass_tiles(a), sms * std::max(1, occ)));
+      return e1;
+    });
+  });
+  if (e != cudaSuccess) return e;
+  return with_tx(a.tx_z, [&](auto T) {
+    return with_occ(a.occ_z, [&](auto O) {
+      constexpr int TX = decltype(T)::value, OCC = decltype(O)::value;
+      int occ = 0;
+      cudaError_t e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_zpass_green<TX, OCC>, kYZThreads,
+                                                                     zpass_smem(a));
+      if (e1 == cudaSuccess) a.grid_z = std::max(1, std::min(zpass_tiles(a), sms * std::max(1, occ)));
+      return e1;
     });
   });
 }
 
 cudaError_t launch_ypass(const CUtensorMap& tm, const IterArgs& a, bool inverse, cudaStream_t s) {
   return with_tx(a.tx_y, [&](auto T) {
-    constexpr int TX = decltype(T)::value;
-    if (inverse)
-      k_ypass<TX, true><<<a.grid_y, kYZThreads, ypass_smem(a), s>>>(tm, a);
-    else
-      k_ypass<TX, false><<<a.grid_y, kYZThreads, ypass_smem(a), s>>>(tm, a);
-    return cudaGetLastError();
+    return with_occ(a.occ_y, [&](auto O) {
+      constexpr int TX = decltype(T)::value, OCC = decltype(O)::value;
+      if (inverse)
+        k_ypass<TX, true, OCC><<<a.grid_y, kYZThreads, ypass_smem(a), s>>>(tm, a);
+      else
+        k_ypass<TX, false, OCC><<<a.grid_y, kYZThreads, ypass_smem(a), s>>>(tm, a);
+      return cudaGetLastError();
+    });
   });
 }
 
 cudaError_t launch_zpass_green(const CUtensorMap& tm, const IterArgs& a, cudaStream_t s) {
   return with_tx(a.tx_z, [&](auto T) {
-    constexpr int TX = decltype(T)::value;
-    k_zpass_green<TX><<<a.grid_z, kYZThreads, zpass_smem(a), s>>>(tm, a);
-    return cudaGetLastError();
+    return with_occ(a.occ_z, [&](auto O) {
+      constexpr int TX = decltype(T)::value, OCC = decltype(O)::value;
+      k_zpass_green<TX, OCC><<<a.grid_z, kYZThreads, zpass_smem(a), s>>>(tm, a);
+      return cudaGetLastError();
+    });
   });
 }
 
@@ -291,15 +339,18 @@ cudaError_t yzpass_set_smem_limit(int bytes) {
   auto set = [&](const void* f) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   };
-  set((const void*)k_ypass<4, false>);
-  set((const void*)k_ypass<4, true>);
-  set((const void*)k_ypass<8, false>);
-  set((const void*)k_ypass<8, true>);
-  set((const void*)k_ypass<16, false>);
-  set((const void*)k_ypass<16, true>);
-  set((const void*)k_zpass_green<4>);
-  set((const void*)k_zpass_green<8>);
-  set((const void*)k_zpass_green<16>);
+  auto set_tx = [&](auto T) {
+    constexpr int TX = decltype(T)::value;
+    set((const void*)k_ypass<TX, false, 1>);
+    set((const void*)k_ypass<TX, true, 1>);
+    set((const void*)k_ypass<TX, false, 2>);
+    set((const void*)k_ypass<TX, true, 2>);
+    set((const void*)k_zpass_green<TX, 1>);
+    set((const void*)k_zpass_green<TX, 2>);
+  };
+  set_tx(std::integral_constant<int, 4>{});
+  set_tx(std::integral_constant<int, 8>{});
+  set_tx(std::integral_constant<int, 16>{});
   return e;
 }
 

@@ -170,7 +170,8 @@ SEED_STREAM = 42
 def serving_stream(n: int, sizes=SERVING_SIZES, seed: int = SEED_STREAM, ppl: int = 8, lam: float = 1.064e-6,
                    p_adjoint: float = 0.5, rate_hz: float | None = None) -> list:
     """Seeded request mix: grid uniform over `sizes` at pitch lam / ppl with one-wavelength
-    absorbing layers on every face, a sphere or a Fresnel lens (equal odds) of index
+    absorbing layers on every face, a centred sphere (radius 1.5 um or 0.3 of the interior,
+    the smaller) or a Fresnel lens (D = 0.7 of the lateral interior), equal odds, of index
     U[1.3, 1.6], an x-polarised plane wave, forward only or forward + adjoint (p_adjoint).
     Each request is a dict; arrivals (Poisson, rate_hz) are added when rate_hz is given."""
     rng = np.random.default_rng(seed)
@@ -202,8 +203,10 @@ def assign_arrivals(reqs: list, rate_hz: float, seed: int = SEED_STREAM):
 
 
 def _sphere_radius(rq) -> float:
+    """1.5 um (the sphere of the 64^3 workload), or 0.3 of the interior if that is smaller:
+    a larger high-index sphere is a resonator the series needs 1e5+ iterations for."""
     inner = min(rq["nx"], rq["ny"], rq["nz"]) - 2 * max(rq["pads"])
-    return 0.3 * inner * rq["pitch"]
+    return min(1.5e-6, 0.3 * inner * rq["pitch"])
 
 
 def _lens_diameter(rq) -> float:

@@ -232,7 +232,7 @@ def run_stream(server: Server, requests: Sequence[dict], make_eps, speed: float 
         while delay > 0:
             results += server.take(64, min(delay, 0.05))
             delay = t0 + rq["arrival_s"] / speed - time.monotonic()
-        server.submit(rq["grid"], eps, rq["source"], rq["r0"], adjoint=rq["adjoint"], tag=rq.get("tag"))
+        server.submit(rq["grid"], eps, rq["source"], rq["r0"], adjoint=rq["adjoint"], tag=rq.get("index"))
         peak = max(peak, server.info()["active"])
     while len(results) < len(requests):
         results += server.take(64, 1.0)
@@ -265,7 +265,16 @@ def main():
     ap.add_argument("--max-active", type=int, default=8)
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--seed", type=int, default=42)
+    ap.add_argument("--verbose", action="store_true", help="one line per result on stderr")
     args = ap.parse_args()
+    import sys
+
+    def log(tag, rq, r):
+        if args.verbose:
+            print(json.dumps({"phase": tag, "grid": [rq["nx"], rq["ny"], rq["nz"]], "adjoint": rq["adjoint"],
+                              "structure": rq["structure"], "status": r.status, "fwd_iters": r.fwd.iters,
+                              "adj_iters": r.adj.iters, "service_s": r.t_done - r.t_admit,
+                              "latency_s": r.latency}), file=sys.stderr, flush=True)
     sizes = [inputs.parse_size(s) for s in args.sizes]
     reqs = [stream_request(rq) for rq in inputs.serving_stream(args.requests, sizes, seed=args.seed, ppl=args.ppl)]
     # single-solve service times of one request per (size, adjoint) class, alone on the GPU
@@ -277,12 +286,15 @@ def main():
                 continue
             srv.submit(rq["grid"], inputs.request_eps(rq), rq["source"], rq["r0"], adjoint=rq["adjoint"])
             r = srv.wait(1)[0]
+            log("alone", rq, r)
             alone[key] = r.t_done - r.t_admit
     mean_service = float(np.mean([alone[(rq["grid"], rq["adjoint"])] for rq in reqs]))
     rate = args.load / mean_service
     inputs.assign_arrivals(reqs, rate, seed=args.seed)
     with Server(max_active=args.max_active, tol=args.tol) as srv:
         rep = run_stream(srv, reqs, inputs.request_eps)
+    for r in rep.results:
+        log("stream", reqs[r.tag], r)
     single = [alone[(rq["grid"], rq["adjoint"])] for rq in reqs]
     print(json.dumps({
         "requests": len(reqs), "sizes": [list(s) for s in sizes], "tol": args.tol, "max_active": args.max_active,
