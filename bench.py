@@ -6,7 +6,10 @@ One step is one design iteration of the paper's method on the Fresnel-lens workl
 lambda/16 with absorbing layers [lambda, lambda, 6 lambda] = [16, 16, 96] voxels per face):
 set the permittivity (potential and splitting), forward solve of the x-polarised plane wave
 to the relative residual --tol, adjoint solve for the focal intensity |E(r0)|^2, gradient.
-The metric is voxels x (forward + adjoint iterations) / time.
+The metric is voxels x (forward + adjoint iterations) / time; ms_per_step is the forward +
+adjoint + gradient time.  After the timed region a short seeded request stream (12 requests
+of 64^3 and 128^3 grids by default) runs through the continuous-batching server, and its
+p50 / p99 latency and solves/s go into the line's "serving" object.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
@@ -265,6 +268,15 @@ def run_gpu(args, rank, world, local_rank):
     cfg.update({"iters_forward": sf.iters, "iters_adjoint": sa.iters, "rel_resid_forward": sf.rel_resid,
                 "rel_resid_adjoint": sa.rel_resid, "objective": obj, "parallelism": f"replicas x{world}",
                 "iteration_ms": iter_ms, "passes": pass_table, "check_every": args.check_every})
+    plan.close()
+    serving = None
+    if args.serve_requests > 0 and args.tol > 0:
+        # served-solve latency (the metric's third part), after the timed region: a seeded
+        # stream of small grids through the continuous-batching server
+        from paper_2506_15411_gb300 import inputs as _in
+        from paper_2506_15411_gb300.serve import measure_stream
+        serving = measure_stream(args.serve_requests, [_in.parse_size(v) for v in args.serve_sizes],
+                                 tol=args.tol)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic", "config": cfg,
@@ -275,9 +287,8 @@ def run_gpu(args, rank, world, local_rank):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * N,
                     "d2h_bytes_per_step": 4 * N + 8, "ms_per_step": e_ms_max / args.steps},
-            "gpu_launches": launches * world, "clocks": clocks}
+            "gpu_launches": launches * world, "clocks": clocks, "serving": serving}
     print(json.dumps(line), flush=True)
-    plan.close()
 
 
 def source_digest():
@@ -319,6 +330,10 @@ def main():
     ap.add_argument("--max-iter", type=int, default=200000)
     ap.add_argument("--check-every", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=12,
+                    help="requests of the served-latency stream after the timed region (0: none; "
+                         "skipped when --tol <= 0)")
+    ap.add_argument("--serve-sizes", nargs="+", default=["64", "128"], help="grid sizes of that stream")
     ap.add_argument("--print-digest", action="store_true", help="print the CUDA source digest and exit")
     args = ap.parse_args()
     if args.print_digest:

@@ -37,87 +37,45 @@ __device__ __forceinline__ float2 stage_inv(const AxisPlan& ap, int q) {
 // the product.
 __device__ __forceinline__ int fdiv(int k, float inv) { return __float2int_rz(((float)k + 0.5f) * inv); }
 
-// tw: the axis' table w_n^m, m < n, in shared memory (copied in with the tile).
-template <int R, bool INV>
+// tw: the axis' table w_n^m, m < n, in shared memory (copied in with the tile).  TW is false
+// for a transform's first stage (Ns = 1: every twiddle is 1) and true for the others, where
+// the butterflies with kk = 0 multiply by w^0 = (1, 0) exactly -- one branch per stage
+// instead of a divergent one per butterfly.
+template <int R, bool INV, bool TW>
 __device__ __forceinline__ void twiddle_dft(float2* v, int kk, int twstep, const float2* tw) {
-  if constexpr (R > 1) {
-    if (kk > 0) {
-      const int step = kk * twstep;
+  if constexpr (R > 1 && TW) {
+    const int step = kk * twstep;
 #pragma unroll
-      for (int r = 1; r < R; ++r) {
-        float2 w = tw[r * step];
-        if (INV) w.y = -w.y;
-        v[r] = cmul(v[r], w);
-      }
+    for (int r = 1; r < R; ++r) {
+      float2 w = tw[r * step];
+      if (INV) w.y = -w.y;
+      v[r] = cmul(v[r], w);
     }
   }
   DFT<R, INV>::run(v);
-}
-
-// ------------------------------------------------------------------- column tiles (y, z)
-template <int R, bool INV, int NCOL>
-__device__ __forceinline__ void stage_cols(const float2* src, float2* dst, int4 g, float invNs,
-                                           const float2* tw, int tid, int nth) {
-  const int stride = g.z, Ns = g.y;
-  const int items = NCOL * stride;
-  for (int k = tid; k < items; k += nth) {
-    const int col = k % NCOL, j = k / NCOL;
-    float2 v[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = src[(j + r * stride) * NCOL + col];
-    const int q = fdiv(j, invNs);
-    const int kk = j - q * Ns;
-    twiddle_dft<R, INV>(v, kk, g.w, tw);
-    const int d = q * Ns * R + kk;
-#pragma unroll
-    for (int r = 0; r < R; ++r) dst[(d + r * Ns) * NCOL + col] = v[r];
-  }
 }
 
 struct NoHook {
   __device__ __forceinline__ void operator()() const {}
 };
 
-// FFT of the NCOL columns held in A, scratch B of the same layout; the result ends in A.
-// `after_first` runs (in every thread) right after the first stage's barrier, when A is no
-// longer read by that stage: the pipelined kernels issue their next prefetch there.
-// Every thread of the block must call it; it ends with a barrier.
-template <bool INV, int NCOL, class Hook = NoHook>
-__device__ __forceinline__ void fft_cols(float2* A, float2* B, const AxisPlan& ap, const float2* tw,
-                                         int tid, int nth, Hook after_first = Hook{}) {
-  const int ns = ap.ns;
-  float2* src = A;
-  float2* dst = B;
-  for (int q = 0; q < ns; ++q) {
-    const int4 g = stage_of(ap, q);
-    const float2 iv = stage_inv(ap, q);
-    float2* out = (q == ns - 1) ? A : dst;
-    radix_dispatch(g.x, [&](auto Ri) {
-      constexpr int R = decltype(Ri)::value;
-      stage_cols<R, INV, NCOL>(src, out, g, iv.y, tw, tid, nth);
-    });
-    __syncthreads();
-    if (q == 0) after_first();
-    float2* t = src;
-    src = dst;
-    dst = t;
-  }
-}
-
 // ------------------------------------------------------------- column tiles, paired, multi-component
-// Element (c, i, col) at base[c * cs + i * NCOL + col].  An item transforms columns 2p and
-// 2p+1 of one component together: 16-byte shared-memory accesses, one twiddle load and one
-// set of index computations for both.  Items run p fastest, then j, then c.
-template <int R, bool INV, int NCOL>
-__device__ __forceinline__ void stage_cols2(const float2* src, float2* dst, int ncomp, int cs, int4 g, float2 iv,
+// Element (c, i, col) at base[c * cs + i * NCOL + col] (c < NCOMP).  An item transforms
+// columns 2p and 2p+1 of one component together: 16-byte shared-memory accesses, one twiddle
+// load and one set of index computations for both.  Items run p fastest, then j, then c.
+template <int R, bool INV, int NCOL, int NCOMP, bool TW>
+__device__ __forceinline__ void stage_cols2(const float2* src, float2* dst, int cs, int4 g, float2 iv,
                                             const float2* tw, int tid, int nth) {
   constexpr int NP = NCOL / 2;
   const int stride = g.z, Ns = g.y;
-  const int items = ncomp * NP * stride;
+  const int items = NCOMP * NP * stride;
   for (int k = tid; k < items; k += nth) {
     const int p = k % NP, rest = k / NP;
-    const int c = fdiv(rest, iv.x);
-    const int j = rest - c * stride;
+    int c = 0, j = rest;
+    if constexpr (NCOMP > 1) {
+      c = fdiv(rest, iv.x);
+      j = rest - c * stride;
+    }
     const float4* s4 = reinterpret_cast<const float4*>(src + c * cs) + p;
     float2 v0[R], v1[R];
 #pragma unroll
@@ -126,18 +84,21 @@ __device__ __forceinline__ void stage_cols2(const float2* src, float2* dst, int 
       v0[r] = make_float2(q.x, q.y);
       v1[r] = make_float2(q.z, q.w);
     }
-    const int qq = fdiv(j, iv.y);
-    const int kk = j - qq * Ns;
-    if constexpr (R > 1) {
-      if (kk > 0) {
-        const int step = kk * g.w;
+    int qq = 0, kk = 0;
+    if constexpr (TW) {
+      qq = fdiv(j, iv.y);
+      kk = j - qq * Ns;
+    } else {
+      qq = j;   // Ns = 1
+    }
+    if constexpr (R > 1 && TW) {
+      const int step = kk * g.w;
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-          float2 w = tw[r * step];
-          if (INV) w.y = -w.y;
-          v0[r] = cmul(v0[r], w);
-          v1[r] = cmul(v1[r], w);
-        }
+      for (int r = 1; r < R; ++r) {
+        float2 w = tw[r * step];
+        if (INV) w.y = -w.y;
+        v0[r] = cmul(v0[r], w);
+        v1[r] = cmul(v1[r], w);
       }
     }
     DFT<R, INV>::run(v0);
@@ -149,15 +110,15 @@ __device__ __forceinline__ void stage_cols2(const float2* src, float2* dst, int 
   }
 }
 
-// Stages [q0, q1) of the transform of ncomp x NCOL columns whose stage-q0 input is in `in`
+// Stages [q0, q1) of the transform of NCOMP x NCOL columns whose stage-q0 input is in `in`
 // (A or B; component stride cs), ping-ponging between A and B; a stage that is the last of
 // the transform writes A (its outputs sit where it read them, so that is safe from either
 // buffer).  Returns the buffer holding the output of stage q1 - 1.  Barrier after each stage;
 // `after_first` runs after the first of them.
-template <bool INV, int NCOL, int MAXR = 16, class Hook = NoHook>
-__device__ __forceinline__ float2* cols2_stages(float2* in, float2* A, float2* B, int ncomp, int cs,
-                                                const AxisPlan& ap, int q0, int q1, const float2* tw, int tid,
-                                                int nth, Hook after_first = Hook{}) {
+template <bool INV, int NCOL, int NCOMP, int MAXR = 16, class Hook = NoHook>
+__device__ __forceinline__ float2* cols2_stages(float2* in, float2* A, float2* B, int cs, const AxisPlan& ap,
+                                                int q0, int q1, const float2* tw, int tid, int nth,
+                                                Hook after_first = Hook{}) {
   float2* src = in;
   for (int q = q0; q < q1; ++q) {
     const int4 g = stage_of(ap, q);
@@ -165,7 +126,10 @@ __device__ __forceinline__ float2* cols2_stages(float2* in, float2* A, float2* B
     float2* out = (q == ap.ns - 1) ? A : (src == A ? B : A);
     radix_dispatch<MAXR>(g.x, [&](auto Ri) {
       constexpr int R = decltype(Ri)::value;
-      stage_cols2<R, INV, NCOL>(src, out, ncomp, cs, g, iv, tw, tid, nth);
+      if (q == 0)
+        stage_cols2<R, INV, NCOL, NCOMP, false>(src, out, cs, g, iv, tw, tid, nth);
+      else
+        stage_cols2<R, INV, NCOL, NCOMP, true>(src, out, cs, g, iv, tw, tid, nth);
     });
     __syncthreads();
     if (q == q0) after_first();
@@ -180,7 +144,7 @@ __device__ __forceinline__ float2* cols2_stages(float2* in, float2* A, float2* B
 // and spreads the stride-R accesses of the early stages (Ns < 16) over all banks.
 __device__ __forceinline__ int swz(int a) { return a ^ ((a >> 4) & 15); }
 
-template <int R, bool INV>
+template <int R, bool INV, bool TW>
 __device__ __forceinline__ void stage_rows(const float2* src, float2* dst, bool sw_in, bool sw_out, int nrows,
                                            int ncomp, int ld, int cs, int4 g, float2 iv,
                                            const float2* tw, int tid, int nth) {
@@ -198,9 +162,12 @@ __device__ __forceinline__ void stage_rows(const float2* src, float2* dst, bool 
       const int a = base + j + r * stride;
       v[r] = src[sw_in ? swz(a) : a];
     }
-    const int q = fdiv(j, iv.y);
-    const int kk = j - q * Ns;
-    twiddle_dft<R, INV>(v, kk, g.w, tw);
+    int q = j, kk = 0;   // Ns = 1 in a first stage
+    if constexpr (TW) {
+      q = fdiv(j, iv.y);
+      kk = j - q * Ns;
+    }
+    twiddle_dft<R, INV, TW>(v, kk, g.w, tw);
     const int d = q * Ns * R + kk;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -230,7 +197,10 @@ __device__ __forceinline__ float2* fft_rows(float2* A, float2* B, int nrows, int
     out = !last ? dst : (q > 0 ? dst : A);
     radix_dispatch<MAXR>(g.x, [&](auto Ri) {
       constexpr int R = decltype(Ri)::value;
-      stage_rows<R, INV>(src, out, q > 0, !last, nrows, ncomp, ld, cs, g, iv, tw, tid, nth);
+      if (q == 0)
+        stage_rows<R, INV, false>(src, out, false, !last, nrows, ncomp, ld, cs, g, iv, tw, tid, nth);
+      else
+        stage_rows<R, INV, true>(src, out, true, !last, nrows, ncomp, ld, cs, g, iv, tw, tid, nth);
     });
     __syncthreads();
     if (q == 0) after_first();

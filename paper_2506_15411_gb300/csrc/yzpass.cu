@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kYZThreads, OCC) k_ypass(const __grid_constant
         issue(tn, nxb, nbar);
       }
     };
-    cols2_stages<INV, TX, MAXR>(cur, cur, scr, 1, 0, a.ay, 0, a.ay.ns, tw, tid, nth, prefetch);
+    cols2_stages<INV, TX, 1, MAXR>(cur, cur, scr, 0, a.ay, 0, a.ay.ns, tw, tid, nth, prefetch);
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {
@@ -126,16 +126,14 @@ __device__ __forceinline__ void stage_last_green(const float2* src, float2* A, i
     for (int c = 0; c < 3; ++c)
 #pragma unroll
       for (int r = 0; r < R; ++r) v[c][r] = src[c * cs + (j + r * stride) * TX + col];
-    // last stage: Ns = n / R = stride, so j mod Ns = j
+    // last stage: Ns = n / R = stride, so j mod Ns = j (j = 0 multiplies by w^0 = 1 exactly)
     if constexpr (R > 1) {
-      if (j > 0) {
-        const int step = j * g.w;
+      const int step = j * g.w;
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-          const float2 w = tw[r * step];
+      for (int r = 1; r < R; ++r) {
+        const float2 w = tw[r * step];
 #pragma unroll
-          for (int c = 0; c < 3; ++c) v[c][r] = cmul(v[c][r], w);
-        }
+        for (int c = 0; c < 3; ++c) v[c][r] = cmul(v[c][r], w);
       }
     }
 #pragma unroll
@@ -234,7 +232,7 @@ __global__ void __launch_bounds__(kYZThreads, OCC) k_zpass_green(const __grid_co
     const float py = two_pi / (float)a.ny * (float)fft_freq(y, a.ny);
     const float qy = (2 * y == a.ny) ? 0.f : py;
     if constexpr (OCC == 1) {
-      float2* P = cols2_stages<false, TX, MAXR>(cur, cur, scr, 3, cs, a.az, 0, ns - 1, tw, tid, nth, prefetch);
+      float2* P = cols2_stages<false, TX, 3, MAXR>(cur, cur, scr, cs, a.az, 0, ns - 1, tw, tid, nth, prefetch);
       const int4 g = stage_of(a.az, ns - 1);
       radix_dispatch<MAXR>(g.x, [&](auto Ri) {
         constexpr int R = decltype(Ri)::value;
@@ -243,11 +241,11 @@ __global__ void __launch_bounds__(kYZThreads, OCC) k_zpass_green(const __grid_co
       __syncthreads();
       if (ns == 1) prefetch();
     } else {
-      cols2_stages<false, TX, MAXR>(cur, cur, scr, 3, cs, a.az, 0, ns, tw, tid, nth, prefetch);
+      cols2_stages<false, TX, 3, MAXR>(cur, cur, scr, cs, a.az, 0, ns, tw, tid, nth, prefetch);
       green_sweep<TX>(cur, cs, x0, py, qy, tid, nth, a);
       __syncthreads();
     }
-    cols2_stages<true, TX, MAXR>(cur, cur, scr, 3, cs, a.az, 0, ns, tw, tid, nth);
+    cols2_stages<true, TX, 3, MAXR>(cur, cur, scr, cs, a.az, 0, ns, tw, tid, nth);
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {

@@ -250,9 +250,45 @@ def stream_request(rq: dict) -> dict:
     return dict(rq, grid=g, source=PlaneWave(pol=rq["pol"]))
 
 
+def measure_stream(requests: int, sizes, ppl: int = 8, load: float = 0.8, max_active: int = 8,
+                   tol: float = 1e-4, seed: int = 42, log=None) -> dict:
+    """Serve a seeded stream (inputs.serving_stream) at `load` times the single-solve service
+    rate and report latency percentiles and throughput, next to the service times of the same
+    request classes solved alone.  log(tag, request, result) sees every result."""
+    from . import inputs
+    reqs = [stream_request(rq) for rq in inputs.serving_stream(requests, sizes, seed=seed, ppl=ppl)]
+    alone = {}
+    with Server(max_active=1, tol=tol) as srv:
+        for rq in reqs:
+            key = (rq["grid"], rq["adjoint"])
+            if key in alone:
+                continue
+            srv.submit(rq["grid"], inputs.request_eps(rq), rq["source"], rq["r0"], adjoint=rq["adjoint"])
+            r = srv.wait(1)[0]
+            if log:
+                log("alone", rq, r)
+            alone[key] = r.t_done - r.t_admit
+    mean_service = float(np.mean([alone[(rq["grid"], rq["adjoint"])] for rq in reqs]))
+    rate = load / mean_service
+    inputs.assign_arrivals(reqs, rate, seed=seed)
+    with Server(max_active=max_active, tol=tol) as srv:
+        rep = run_stream(srv, reqs, inputs.request_eps)
+    if log:
+        for r in rep.results:
+            log("stream", reqs[r.tag], r)
+    single = [alone[(rq["grid"], rq["adjoint"])] for rq in reqs]
+    return {"requests": len(reqs), "sizes": [list(v) for v in sizes], "tol": tol, "max_active": max_active,
+            "arrival_rate_hz": rate, "offered_load": load,
+            "p50_latency_s": rep.p50_s, "p99_latency_s": rep.p99_s, "mean_latency_s": rep.mean_s,
+            "solves_per_s": rep.solves_per_s, "makespan_s": rep.makespan_s, "peak_active": rep.peak_active,
+            "single_solve_p50_s": percentile(single, 50), "single_solve_p99_s": percentile(single, 99),
+            "failed": sum(1 for r in rep.results if not r.ok)}
+
+
 def main():
     import argparse
     import json
+    import sys
 
     from . import inputs
 
@@ -267,7 +303,6 @@ def main():
     ap.add_argument("--seed", type=int, default=42)
     ap.add_argument("--verbose", action="store_true", help="one line per result on stderr")
     args = ap.parse_args()
-    import sys
 
     def log(tag, rq, r):
         if args.verbose:
@@ -275,34 +310,10 @@ def main():
                               "structure": rq["structure"], "status": r.status, "fwd_iters": r.fwd.iters,
                               "adj_iters": r.adj.iters, "service_s": r.t_done - r.t_admit,
                               "latency_s": r.latency}), file=sys.stderr, flush=True)
-    sizes = [inputs.parse_size(s) for s in args.sizes]
-    reqs = [stream_request(rq) for rq in inputs.serving_stream(args.requests, sizes, seed=args.seed, ppl=args.ppl)]
-    # single-solve service times of one request per (size, adjoint) class, alone on the GPU
-    alone = {}
-    with Server(max_active=1, tol=args.tol) as srv:
-        for rq in reqs:
-            key = (rq["grid"], rq["adjoint"])
-            if key in alone:
-                continue
-            srv.submit(rq["grid"], inputs.request_eps(rq), rq["source"], rq["r0"], adjoint=rq["adjoint"])
-            r = srv.wait(1)[0]
-            log("alone", rq, r)
-            alone[key] = r.t_done - r.t_admit
-    mean_service = float(np.mean([alone[(rq["grid"], rq["adjoint"])] for rq in reqs]))
-    rate = args.load / mean_service
-    inputs.assign_arrivals(reqs, rate, seed=args.seed)
-    with Server(max_active=args.max_active, tol=args.tol) as srv:
-        rep = run_stream(srv, reqs, inputs.request_eps)
-    for r in rep.results:
-        log("stream", reqs[r.tag], r)
-    single = [alone[(rq["grid"], rq["adjoint"])] for rq in reqs]
-    print(json.dumps({
-        "requests": len(reqs), "sizes": [list(s) for s in sizes], "tol": args.tol, "max_active": args.max_active,
-        "arrival_rate_hz": rate, "offered_load": args.load,
-        "p50_latency_s": rep.p50_s, "p99_latency_s": rep.p99_s, "mean_latency_s": rep.mean_s,
-        "solves_per_s": rep.solves_per_s, "makespan_s": rep.makespan_s, "peak_active": rep.peak_active,
-        "single_solve_p50_s": percentile(single, 50), "single_solve_p99_s": percentile(single, 99),
-        "failed": sum(1 for r in rep.results if not r.ok)}))
+
+    sizes = [inputs.parse_size(v) for v in args.sizes]
+    print(json.dumps(measure_stream(args.requests, sizes, args.ppl, args.load, args.max_active, args.tol,
+                                    args.seed, log)))
 
 
 if __name__ == "__main__":
