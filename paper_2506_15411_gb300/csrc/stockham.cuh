@@ -21,6 +21,8 @@
 #include "cbs_internal.h"
 #include "fft_radix.cuh"
 
+#include <type_traits>
+
 namespace cbs {
 
 constexpr int kMaxRadix = 16;
@@ -70,7 +72,7 @@ __device__ __forceinline__ void stage_cols2(const float2* src, float2* dst, int 
   const int stride = g.z, Ns = g.y;
   const int items = NCOMP * NP * stride;
   for (int k = tid; k < items; k += nth) {
-    const int p = k % NP, rest = k / NP;
+    const int p = (int)((unsigned)k % NP), rest = (int)((unsigned)k / NP);
     int c = 0, j = rest;
     if constexpr (NCOMP > 1) {
       c = fdiv(rest, iv.x);
@@ -144,10 +146,23 @@ __device__ __forceinline__ float2* cols2_stages(float2* in, float2* A, float2* B
 // and spreads the stride-R accesses of the early stages (Ns < 16) over all banks.
 __device__ __forceinline__ int swz(int a) { return a ^ ((a >> 4) & 15); }
 
-template <int R, bool INV, bool TW>
+// Element hooks of a row transform.  Pre(c, row, x, v) gives the value the first stage uses
+// for input element (c, row, x) (the forward x pass forms V E + S there, as it loads);
+// Post(c, row, x, v) takes output element (c, row, x) of the last stage instead of a store
+// (the inverse x pass updates E there).  NoPre / NoPost: plain loads and stores.
+struct NoPre {
+  __device__ __forceinline__ float2 operator()(int, int, int, float2 v) const { return v; }
+};
+struct NoPost {
+  __device__ __forceinline__ void operator()(int, int, int, float2) const {}
+};
+
+template <int R, bool INV, bool TW, class Pre, class Post>
 __device__ __forceinline__ void stage_rows(const float2* src, float2* dst, bool sw_in, bool sw_out, int nrows,
                                            int ncomp, int ld, int cs, int4 g, float2 iv,
-                                           const float2* tw, int tid, int nth) {
+                                           const float2* tw, int tid, int nth, Pre pre, Post post) {
+  constexpr bool kPre = !std::is_same<Pre, NoPre>::value;
+  constexpr bool kPost = !std::is_same<Post, NoPost>::value;
   const int stride = g.z, Ns = g.y;
   const int items = ncomp * nrows * stride;
   const float inv_rows = 1.0f / (float)nrows;
@@ -161,6 +176,7 @@ __device__ __forceinline__ void stage_rows(const float2* src, float2* dst, bool 
     for (int r = 0; r < R; ++r) {
       const int a = base + j + r * stride;
       v[r] = src[sw_in ? swz(a) : a];
+      if constexpr (kPre) v[r] = pre(c, row, j + r * stride, v[r]);
     }
     int q = j, kk = 0;   // Ns = 1 in a first stage
     if constexpr (TW) {
@@ -171,21 +187,26 @@ __device__ __forceinline__ void stage_rows(const float2* src, float2* dst, bool 
     const int d = q * Ns * R + kk;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const int a = base + d + r * Ns;
-      dst[sw_out ? swz(a) : a] = v[r];
+      if constexpr (kPost) {
+        post(c, row, d + r * Ns, v[r]);
+      } else {
+        const int a = base + d + r * Ns;
+        dst[sw_out ? swz(a) : a] = v[r];
+      }
     }
   }
 }
 
 // FFT of nrows rows of ncomp components held in A (component stride cs, row stride ld; cs,
-// ld and the base of A multiples of 16), scratch B of the same layout.  Returns the buffer
-// holding the (unswizzled) result: A, or B when the last of several stages reads A (its
-// swizzled reads and unswizzled writes must not share a buffer).  `after_first` as for
-// fft_cols.  Ends with a barrier.
-template <bool INV, int MAXR = 16, class Hook = NoHook>
+// ld and the base of A multiples of 16), scratch B of the same layout, with the element hooks
+// pre (first stage) and post (last stage).  Returns the buffer holding the (unswizzled)
+// result: A, or B when the last of several stages reads A (its swizzled reads and
+// unswizzled writes must not share a buffer); nothing is stored when post is not NoPost.
+// `after_first` runs in every thread after the first stage's barrier.  Ends with a barrier.
+template <bool INV, int MAXR = 16, class Pre = NoPre, class Post = NoPost, class Hook = NoHook>
 __device__ __forceinline__ float2* fft_rows(float2* A, float2* B, int nrows, int ncomp, int ld, int cs,
                                             const AxisPlan& ap, const float2* tw, int tid, int nth,
-                                            Hook after_first = Hook{}) {
+                                            Pre pre = Pre{}, Post post = Post{}, Hook after_first = Hook{}) {
   const int ns = ap.ns;
   float2* src = A;
   float2* dst = B;
@@ -197,10 +218,14 @@ __device__ __forceinline__ float2* fft_rows(float2* A, float2* B, int nrows, int
     out = !last ? dst : (q > 0 ? dst : A);
     radix_dispatch<MAXR>(g.x, [&](auto Ri) {
       constexpr int R = decltype(Ri)::value;
-      if (q == 0)
-        stage_rows<R, INV, false>(src, out, false, !last, nrows, ncomp, ld, cs, g, iv, tw, tid, nth);
+      if (q == 0 && last)
+        stage_rows<R, INV, false>(src, out, false, false, nrows, ncomp, ld, cs, g, iv, tw, tid, nth, pre, post);
+      else if (q == 0)
+        stage_rows<R, INV, false>(src, out, false, true, nrows, ncomp, ld, cs, g, iv, tw, tid, nth, pre, NoPost{});
+      else if (last)
+        stage_rows<R, INV, true>(src, out, true, false, nrows, ncomp, ld, cs, g, iv, tw, tid, nth, NoPre{}, post);
       else
-        stage_rows<R, INV, true>(src, out, true, !last, nrows, ncomp, ld, cs, g, iv, tw, tid, nth);
+        stage_rows<R, INV, true>(src, out, true, true, nrows, ncomp, ld, cs, g, iv, tw, tid, nth, NoPre{}, NoPost{});
     });
     __syncthreads();
     if (q == 0) after_first();

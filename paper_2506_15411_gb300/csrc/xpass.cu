@@ -1,9 +1,11 @@
 // xpass.cu -- the two passes along x (contiguous rows) of one CBS iteration.
 //
 //   forward:  W_c = FFT_x(V E_c + S_c)                       (scattering potential and source
-//                                                              applied in shared memory)
+//                                                              applied as the first FFT stage
+//                                                              loads each element)
 //   inverse:  W_c = IFFT_x(W_c);  delta_c = gamma (E_c - W_c);  E_c -= delta_c;
-//             sum |delta|^2 in FP64                           (update of the preconditioned
+//             sum |delta|^2 in FP64, the update applied as the last inverse stage produces
+//             each element                                    (update of the preconditioned
 //                                                              series, refs. [25], [26] of
 //                                                              arXiv 2506.15411)
 // A block owns a tile of `rpb` consecutive rows (z, y) of all three components.  Its rows are
@@ -120,7 +122,7 @@ __device__ __forceinline__ int x_tiles(const IterArgs& a) { return (a.ny * a.nz 
 // during the next tile.
 __global__ void __launch_bounds__(kThreads, 1) k_xpass_fwd(const IterArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int rpb = a.rpb, nxp = a.nxp, n = a.nx;
+  const int rpb = a.rpb, nxp = a.nxp;
   const int span = rpb * nxp;
   const int rows = a.ny * a.nz, ntiles = x_tiles(a);
   XTile t = carve(smem_raw, rpb, nxp, a.twbx, false);
@@ -128,7 +130,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_xpass_fwd(const IterArgs a) {
   if (tile >= ntiles) return;
   if (!block_setup_n(t.in0, t.full, 2, t.fail, a.err)) return;
   const int tid = threadIdx.x, nth = blockDim.x;
-  const float inv_n = 1.0f / (float)n, inv_ny = 1.0f / (float)a.ny;
+  const float inv_ny = 1.0f / (float)a.ny;
   auto issue = [&](int tt, int k, uint32_t extra) {
     const int r0 = tt * rpb, nr = min(rpb, rows - r0);
     const uint32_t bytes = (uint32_t)(nr * nxp * sizeof(float2));
@@ -147,24 +149,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_xpass_fwd(const IterArgs a) {
     if (!block_wait(&t.full[k], t.fail, a.err, (uint32_t)((i >> 1) & 1))) return;
     float2* in = t.in0 + k * t.set;
     const float2* v = t.v0 + k * t.set;
-    // V E + S in place (the row padding stays as loaded)
-    for (int q = tid; q < nr * n; q += nth) {
-      const int row = fdiv(q, inv_n), x = q - row * n;
+    // V E + S, formed as the first FFT stage loads each element
+    auto pre = [&](int c, int row, int x, float2 e) {
       const int gr = r0 + row;
       const int z = fdiv(gr, inv_ny), y = gr - z * a.ny;
-      const int o = row * nxp + x;
-      const float2 vv = v[o];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) in[c * span + o] = cadd(cmul(vv, in[c * span + o]), source_at(a, c, z, y, x));
-    }
-    __syncthreads();
+      return cadd(cmul(v[row * nxp + x], e), source_at(a, c, z, y, x));
+    };
     auto prefetch = [&] {
       if (tid == 0 && tn < ntiles) {
         bulk_wait_read_all();   // the store of tile i-1 (from set k^1) has left shared memory
         issue(tn, k ^ 1, 0);
       }
     };
-    const float2* w = fft_rows<false>(in, t.scr + k * t.set, nr, 3, nxp, span, a.ax, t.tw, tid, nth, prefetch);
+    const float2* w = fft_rows<false>(in, t.scr + k * t.set, nr, 3, nxp, span, a.ax, t.tw, tid, nth, pre, NoPost{},
+                                      prefetch);
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {
@@ -179,7 +177,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_xpass_fwd(const IterArgs a) {
 // Persistent, double-buffered inverse x pass with the update and the FP64 residual.
 __global__ void __launch_bounds__(kThreads, 1) k_xpass_inv_update(const IterArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int rpb = a.rpb, nxp = a.nxp, n = a.nx;
+  const int rpb = a.rpb, nxp = a.nxp;
   const int span = rpb * nxp;
   const int rows = a.ny * a.nz, ntiles = x_tiles(a);
   XTile t = carve(smem_raw, rpb, nxp, a.twbx, true);
@@ -203,7 +201,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_xpass_inv_update(const IterArgs
       bulk_load(t.tw, a.twx, a.twbx, &t.full[0]);
     }
     const float ie = a.inv_eps;
-    const float inv_n = 1.0f / (float)n;
     for (int i = 0; tile < ntiles; ++i, tile += gridDim.x) {
       const int k = i & 1;
       const int r0 = tile * rpb, nr = min(rpb, rows - r0);
@@ -215,22 +212,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_xpass_inv_update(const IterArgs
           issue(tn, k ^ 1, 0);
         }
       };
-      const float2* w = fft_rows<true>(t.in0 + k * t.set, t.scr, nr, 3, nxp, span, a.ax, t.tw, tid, nth, prefetch);
       float2* e = t.e0 + k * t.set;
       const float2* v = t.v0 + k * t.set;
-      for (int q = tid; q < nr * n; q += nth) {
-        const int row = fdiv(q, inv_n), x = q - row * n;
+      // the update, applied as the last inverse-FFT stage produces each W element:
+      // delta = gamma (E - W), gamma = (i / epsilon) V; E -= delta; acc += |delta|^2
+      auto post = [&](int c, int row, int x, float2 w) {
         const int o = row * nxp + x;
         const float2 vv = v[o];
-        const float2 g = make_float2(-vv.y * ie, vv.x * ie);   // gamma = (i / epsilon) V
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float2 ec = e[c * span + o];
-          const float2 d = cmul(g, csub(ec, w[c * span + o]));
-          e[c * span + o] = csub(ec, d);
-          acc = fmaf(d.x, d.x, fmaf(d.y, d.y, acc));
-        }
-      }
+        const float2 g = make_float2(-vv.y * ie, vv.x * ie);
+        const float2 ec = e[c * span + o];
+        const float2 d = cmul(g, csub(ec, w));
+        e[c * span + o] = csub(ec, d);
+        acc = fmaf(d.x, d.x, fmaf(d.y, d.y, acc));
+      };
+      fft_rows<true>(t.in0 + k * t.set, t.scr, nr, 3, nxp, span, a.ax, t.tw, tid, nth, NoPre{}, post, prefetch);
       fence_async_smem();
       __syncthreads();
       if (tid == 0) {

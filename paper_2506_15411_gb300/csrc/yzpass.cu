@@ -120,7 +120,7 @@ __device__ __forceinline__ void stage_last_green(const float2* src, float2* A, i
   const int items = TX * stride;
   const float two_pi = 6.283185307179586f;
   for (int k = tid; k < items; k += nth) {
-    const int col = k % TX, j = k / TX;
+    const int col = (int)((unsigned)k % TX), j = (int)((unsigned)k / TX);
     float2 v[3][R];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
@@ -162,7 +162,7 @@ __device__ __forceinline__ void green_sweep(float2* A, int cs, int x0, float py,
   const float two_pi = 6.283185307179586f;
   const float kx = two_pi / (float)a.nx, kz = two_pi / (float)a.nz;
   for (int k = tid; k < TX * a.nz; k += nth) {
-    const int col = k % TX, iz = k / TX;
+    const int col = (int)((unsigned)k % TX), iz = (int)((unsigned)k / TX);
     const int x = x0 + col;
     const float px = kx * (float)fft_freq(x, a.nx);
     const float qx = (2 * x == a.nx) ? 0.f : px;
