@@ -160,6 +160,19 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def combine_ranks(times_ms, counts, world, device):
+    """Replicas: the slowest rank's time of each timed region (max) and the work of all ranks
+    (sum); with one rank, the inputs.  Returns (times, counts) as lists."""
+    import torch
+    tmax = torch.tensor(times_ms, dtype=torch.float64, device=device)
+    tsum = torch.tensor(counts, dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return tmax.tolist(), tsum.tolist()
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -231,13 +244,8 @@ def run_gpu(args, rank, world, local_rank):
     barrier()
     e_ms = e0.elapsed_time(e1)
 
-    tmax = torch.tensor([ms, e_ms], dtype=torch.float64, device=dev)
-    tsum = torch.tensor([float(iters), float(e_iters)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-    ms_max, e_ms_max = tmax.tolist()
-    iters_all, e_iters_all = tsum.tolist()
+    (ms_max, e_ms_max), (iters_all, e_iters_all) = combine_ranks([ms, e_ms], [float(iters), float(e_iters)],
+                                                                 world, dev)
     if rank != 0:
         plan.close()
         return
