@@ -146,12 +146,15 @@ int cbs_design_step_host(cbs_plan_t plan, const float* eps_host, const cbs_sourc
                          const int r0[3], float* grad_host, double* objective,
                          cbs_stats* fwd, cbs_stats* adj);
 
-/* Pass timing.  With profiling on, each block of iterations records CUDA events on the
- * plan's stream around the five launches of its last iteration (also inside the replayed
- * graphs); cbs_pass_times returns, per pass (0 x forward, 1 y forward, 2 z + k-space
- * multiply, 3 y inverse, 4 x inverse + update), the summed event time in ms and the number
- * of timed launches since the last reset.  Toggling drops the cached graphs.  Errors:
- * CBS_ERR_ARG, CBS_ERR_CUDA. */
+/* Pass timing.  A series launches the forward x pass (V E + S, FFT_x) once, then four
+ * kernels per iteration: y forward, z + k-space multiply, y inverse, and an x pass that
+ * finishes the iteration (IFFT_x, update, residual) and forms the next iteration's FFT_x of
+ * V E + S.  With profiling on, each block of iterations records CUDA events on the plan's
+ * stream around the four launches of its last iteration (kept out of the captured graphs);
+ * cbs_pass_times returns, per slot (0 the series' first forward x pass -- not timed, always 0;
+ * 1 y forward; 2 z + k-space multiply; 3 y inverse; 4 x inverse + update + next forward x),
+ * the summed event time in ms and the number of timed launches since the last reset.
+ * Toggling drops the cached graphs.  Errors: CBS_ERR_ARG, CBS_ERR_CUDA. */
 int cbs_set_profiling(cbs_plan_t plan, int on);
 int cbs_pass_times(cbs_plan_t plan, double ms_total[5], long long launches[5], int reset);
 

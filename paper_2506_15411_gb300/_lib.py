@@ -33,7 +33,9 @@ EXPORTS = ("cbs_plan", "cbs_set_permittivity", "cbs_get_splitting", "cbs_set_sol
            "cbs_design_permittivity", "cbs_design_height_gradient", "cbs_design_adam", "cbs_design_step",
            "cbs_server_create", "cbs_server_destroy", "cbs_server_submit", "cbs_server_take", "cbs_server_info")
 
-PASS_NAMES = ("k_xpass_fwd", "k_ypass_fwd", "k_zpass_green", "k_ypass_inv", "k_xpass_inv_update")
+# cbs_pass_times slots: the series' first forward x pass (launched once per series, not
+# timed), then the four kernels of every iteration
+PASS_NAMES = ("k_xpass_fwd", "k_ypass_fwd", "k_zpass_green", "k_ypass_inv", "k_xpass_inv_fwd")
 
 
 class cbs_plan_desc(Structure):

@@ -1,13 +1,15 @@
 // api.cu -- host side of the C ABI declared in include/cbs.h: plans, the iteration loop with
 // its residual checks, the adjoint and gradient calls.
 //
-// One CBS iteration (refs. [25], [26] of arXiv 2506.15411) is five kernel launches on the
+// One CBS iteration (refs. [25], [26] of arXiv 2506.15411) is these kernel passes on the
 // plan's stream:
 //   1. x pass     W = FFT_x(V E + S)
 //   2. y pass     W = FFT_y(W)
 //   3. z pass     W = IFFT_z(G(p) FFT_z(W)) / N
 //   4. y pass     W = IFFT_y(W)
 //   5. x pass     W = IFFT_x(W); delta = gamma (E - W); E -= delta; sum |delta|^2 (FP64)
+// where pass 5 of one iteration and pass 1 of the next run as one kernel on each x tile, so a
+// series launches pass 1 once and then four kernels per iteration.
 // Every `check_every` iterations the host reads the FP64 residual sums and decides whether
 // to stop; a full block of iterations is replayed from a CUDA graph.
 #include <cuda.h>
@@ -202,19 +204,19 @@ int sync_in(cbs_plan_s* p) {
   return CBS_OK;
 }
 
-// The five launches of one iteration; with ev != null, events ev[0..5] bracket them.
+// The four launches of one iteration after the series' first (which k_xpass_fwd starts):
+// y, z + Green, inverse y, then the x pass that finishes this iteration and forms the next
+// one's W.  With ev != null, events ev[0..4] bracket them.
 int launch_iteration(const cbs_plan_s* p, const IterArgs& a, cudaStream_t s, cudaEvent_t* ev) {
   if (ev) CK(cudaEventRecord(ev[0], s));
-  CK(launch_xpass_fwd(a, s));
-  if (ev) CK(cudaEventRecord(ev[1], s));
   CK(launch_ypass(p->tmy, a, false, s));
-  if (ev) CK(cudaEventRecord(ev[2], s));
+  if (ev) CK(cudaEventRecord(ev[1], s));
   CK(launch_zpass_green(p->tmz, a, s));
-  if (ev) CK(cudaEventRecord(ev[3], s));
+  if (ev) CK(cudaEventRecord(ev[2], s));
   CK(launch_ypass(p->tmy, a, true, s));
+  if (ev) CK(cudaEventRecord(ev[3], s));
+  CK(launch_xpass_inv_fwd(a, s));
   if (ev) CK(cudaEventRecord(ev[4], s));
-  CK(launch_xpass_inv_update(a, s));
-  if (ev) CK(cudaEventRecord(ev[5], s));
   return CBS_OK;
 }
 
@@ -233,11 +235,11 @@ int launch_range(cbs_plan_s* p, const IterArgs& a0, int k0, int k1, int m) {
 // After a block has completed: add its timed iteration to the per-pass totals.
 int collect_pass_times(cbs_plan_s* p) {
   if (!p->profiling) return CBS_OK;
-  for (int i = 0; i < 5; ++i) {
+  for (int i = 0; i < 4; ++i) {   // passes 1..4; pass 0 (the first forward x) is not timed
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, p->pev[i], p->pev[i + 1]));
-    p->pass_ms[i] += ms;
-    p->pass_n[i] += 1;
+    p->pass_ms[i + 1] += ms;
+    p->pass_n[i + 1] += 1;
   }
   return CBS_OK;
 }
@@ -407,7 +409,8 @@ void series_begin(cbs_plan_s* p, float2* E, const SourceArgs& src, int warm, Ser
   if (warm == 2) {
     IterArgs a1 = R.a;
     a1.slot = 0;
-    int rc = launch_iteration(p, a1, p->stream, nullptr);
+    int rc = launch_xpass_fwd(a1, p->stream) == cudaSuccess ? CBS_OK : fail(CBS_ERR_CUDA, "x pass launch failed");
+    if (!rc) rc = launch_iteration(p, a1, p->stream, nullptr);
     if (!rc) {
       e = cudaMemcpyAsync(p->hist_host, p->hist, sizeof(double), cudaMemcpyDeviceToHost, p->stream);
       if (e == cudaSuccess) e = cudaMemcpyAsync(p->err_host, p->err_dev, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
@@ -429,6 +432,7 @@ void series_begin(cbs_plan_s* p, float2* E, const SourceArgs& src, int warm, Ser
   if (warm && e == cudaSuccess)
     e = cudaMemcpy2DAsync(p->Ei, pad_row_bytes(p), E, dense_row_bytes(p), dense_row_bytes(p), field_rows(p),
                           cudaMemcpyDeviceToDevice, p->stream);
+  if (e == cudaSuccess) e = launch_xpass_fwd(R.a, p->stream);   // W of the first iteration
   if (e != cudaSuccess) {
     R.rc = fail(CBS_ERR_CUDA, "field copy-in: %s", cudaGetErrorString(e));
     R.finished = true;

@@ -73,7 +73,7 @@ struct IterArgs {
 cudaError_t launch_xpass_fwd(const IterArgs& a, cudaStream_t s);   // W = FFTx(V E + S)
 cudaError_t launch_ypass(const CUtensorMap& tm, const IterArgs& a, bool inverse, cudaStream_t s);
 cudaError_t launch_zpass_green(const CUtensorMap& tm, const IterArgs& a, cudaStream_t s);  // FFTz, G, IFFTz
-cudaError_t launch_xpass_inv_update(const IterArgs& a, cudaStream_t s);  // IFFTx, update, residual
+cudaError_t launch_xpass_inv_fwd(const IterArgs& a, cudaStream_t s);  // IFFTx, update, residual, next FFTx
 
 // Shared-memory bytes and threads of each pass for the plan's shapes.
 size_t xpass_smem(const IterArgs& a);

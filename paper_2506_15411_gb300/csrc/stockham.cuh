@@ -156,12 +156,27 @@ struct NoPre {
 struct NoPost {
   __device__ __forceinline__ void operator()(int, int, int, float2) const {}
 };
+// A Pre hook that makes its value from (c, row, x) alone: the first stage does not load its
+// input from the tile (the fused x pass forms V E + S from another buffer).
+template <class F>
+struct Generate {
+  F f;
+  static constexpr bool kGenerates = true;
+  __device__ __forceinline__ float2 operator()(int c, int row, int x, float2) const { return f(c, row, x); }
+};
+template <class F>
+__device__ __forceinline__ Generate<F> generate(F f) { return Generate<F>{f}; }
+template <class P, class = void>
+struct generates : std::false_type {};
+template <class P>
+struct generates<P, std::void_t<decltype(P::kGenerates)>> : std::bool_constant<P::kGenerates> {};
 
 template <int R, bool INV, bool TW, class Pre, class Post>
 __device__ __forceinline__ void stage_rows(const float2* src, float2* dst, bool sw_in, bool sw_out, int nrows,
                                            int ncomp, int ld, int cs, int4 g, float2 iv,
                                            const float2* tw, int tid, int nth, Pre pre, Post post) {
   constexpr bool kPre = !std::is_same<Pre, NoPre>::value;
+  constexpr bool kGen = generates<Pre>::value;
   constexpr bool kPost = !std::is_same<Post, NoPost>::value;
   const int stride = g.z, Ns = g.y;
   const int items = ncomp * nrows * stride;
@@ -174,9 +189,13 @@ __device__ __forceinline__ void stage_rows(const float2* src, float2* dst, bool 
     float2 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const int a = base + j + r * stride;
-      v[r] = src[sw_in ? swz(a) : a];
-      if constexpr (kPre) v[r] = pre(c, row, j + r * stride, v[r]);
+      if constexpr (kGen) {
+        v[r] = pre(c, row, j + r * stride, make_float2(0.f, 0.f));
+      } else {
+        const int a = base + j + r * stride;
+        v[r] = src[sw_in ? swz(a) : a];
+        if constexpr (kPre) v[r] = pre(c, row, j + r * stride, v[r]);
+      }
     }
     int q = j, kk = 0;   // Ns = 1 in a first stage
     if constexpr (TW) {

@@ -1,13 +1,14 @@
-// xpass.cu -- the two passes along x (contiguous rows) of one CBS iteration.
+// xpass.cu -- the passes along x (contiguous rows) of the CBS iterations.
 //
 //   forward:  W_c = FFT_x(V E_c + S_c)                       (scattering potential and source
 //                                                              applied as the first FFT stage
 //                                                              loads each element)
-//   inverse:  W_c = IFFT_x(W_c);  delta_c = gamma (E_c - W_c);  E_c -= delta_c;
+//   inverse + next forward (one kernel):
+//             W_c = IFFT_x(W_c);  delta_c = gamma (E_c - W_c);  E_c -= delta_c;
 //             sum |delta|^2 in FP64, the update applied as the last inverse stage produces
-//             each element                                    (update of the preconditioned
-//                                                              series, refs. [25], [26] of
-//                                                              arXiv 2506.15411)
+//             each element (update of the preconditioned series, refs. [25], [26] of
+//             arXiv 2506.15411); then W_c = FFT_x(V E_c + S_c) of the next iteration from
+//             the E just updated, while the tile is still on chip
 // A block owns a tile of `rpb` consecutive rows (z, y) of all three components.  Its rows are
 // contiguous in the padded layouts of E, V and W (row pitch nxp, 16 complex values), so the
 // tile arrives with one bulk copy (cp.async.bulk) per array and component and leaves the same
@@ -174,8 +175,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_xpass_fwd(const IterArgs a) {
   if (tid == 0) bulk_wait_all();
 }
 
-// Persistent, double-buffered inverse x pass with the update and the FP64 residual.
-__global__ void __launch_bounds__(kThreads, 1) k_xpass_inv_update(const IterArgs a) {
+// Persistent, double-buffered x pass that ends one iteration and starts the next on each
+// tile: the inverse x transform with the update and the FP64 residual, the store of E, then
+// the forward x transform of V E + S of the next iteration (formed from the updated E as its
+// first stage computes its inputs) and the store of W.  The series' first iteration runs
+// k_xpass_fwd before it; after the last one the W it leaves is not used.
+__global__ void __launch_bounds__(kThreads, 1) k_xpass_inv_fwd(const IterArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int rpb = a.rpb, nxp = a.nxp;
   const int span = rpb * nxp;
@@ -201,6 +206,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_xpass_inv_update(const IterArgs
       bulk_load(t.tw, a.twx, a.twbx, &t.full[0]);
     }
     const float ie = a.inv_eps;
+    const float inv_ny = 1.0f / (float)a.ny;
+    // the forward transform's ping-pong buffers, ordered so that its result lands in the
+    // tile's W buffer (an odd number of stages >= 3 ends in the second one)
+    const bool res_in_b = (a.ax.ns % 2 == 1) && a.ax.ns >= 3;
     for (int i = 0; tile < ntiles; ++i, tile += gridDim.x) {
       const int k = i & 1;
       const int r0 = tile * rpb, nr = min(rpb, rows - r0);
@@ -225,12 +234,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_xpass_inv_update(const IterArgs
         e[c * span + o] = csub(ec, d);
         acc = fmaf(d.x, d.x, fmaf(d.y, d.y, acc));
       };
-      fft_rows<true>(t.in0 + k * t.set, t.scr, nr, 3, nxp, span, a.ax, t.tw, tid, nth, NoPre{}, post, prefetch);
+      float2* win = t.in0 + k * t.set;
+      fft_rows<true>(win, t.scr, nr, 3, nxp, span, a.ax, t.tw, tid, nth, NoPre{}, post, prefetch);
+      fence_async_smem();
+      __syncthreads();
+      const uint32_t bytes = (uint32_t)(nr * nxp * sizeof(float2));
+      if (tid == 0) {
+        for (int c = 0; c < 3; ++c) bulk_store(a.E + c * a.Nw + (size_t)r0 * nxp, e + c * span, bytes);
+        bulk_commit();
+      }
+      // next iteration: W = FFT_x(V E + S) from the updated E (read while its store drains)
+      auto gen = generate([&](int c, int row, int x) {
+        const int gr = r0 + row;
+        const int z = fdiv(gr, inv_ny), y = gr - z * a.ny;
+        const int o = row * nxp + x;
+        return cadd(cmul(v[o], e[c * span + o]), source_at(a, c, z, y, x));
+      });
+      const float2* w = fft_rows<false>(res_in_b ? t.scr : win, res_in_b ? win : t.scr, nr, 3, nxp, span, a.ax,
+                                        t.tw, tid, nth, gen, NoPost{});
       fence_async_smem();
       __syncthreads();
       if (tid == 0) {
-        const uint32_t bytes = (uint32_t)(nr * nxp * sizeof(float2));
-        for (int c = 0; c < 3; ++c) bulk_store(a.E + c * a.Nw + (size_t)r0 * nxp, e + c * span, bytes);
+        for (int c = 0; c < 3; ++c) bulk_store(a.W + c * a.Nw + (size_t)r0 * nxp, w + c * span, bytes);
         bulk_commit();
       }
     }
@@ -257,7 +282,7 @@ cudaError_t x_grid_size(IterArgs& a, int sms) {
   int occ_f = 0, occ_i = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, k_xpass_fwd, kThreads, xpass_fwd_smem(a));
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_i, k_xpass_inv_update, kThreads, xpass_smem(a));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_i, k_xpass_inv_fwd, kThreads, xpass_smem(a));
   if (e != cudaSuccess) return e;
   a.grid_x = std::max(1, std::min(xpass_tiles(a), sms * std::max(1, occ_i)));
   a.grid_xf = std::max(1, std::min(xpass_tiles(a), sms * std::max(1, occ_f)));
@@ -269,15 +294,15 @@ cudaError_t launch_xpass_fwd(const IterArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_xpass_inv_update(const IterArgs& a, cudaStream_t s) {
-  k_xpass_inv_update<<<a.grid_x, kThreads, xpass_smem(a), s>>>(a);
+cudaError_t launch_xpass_inv_fwd(const IterArgs& a, cudaStream_t s) {
+  k_xpass_inv_fwd<<<a.grid_x, kThreads, xpass_smem(a), s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t xpass_set_smem_limit(int bytes) {
   cudaError_t e = cudaFuncSetAttribute(k_xpass_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_xpass_inv_update, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return cudaFuncSetAttribute(k_xpass_inv_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 }  // namespace cbs
