@@ -7,9 +7,10 @@ lambda/16 with absorbing layers [lambda, lambda, 6 lambda] = [16, 16, 96] voxels
 set the permittivity (potential and splitting), forward solve of the x-polarised plane wave
 to the relative residual --tol, adjoint solve for the focal intensity |E(r0)|^2, gradient.
 The metric is voxels x (forward + adjoint iterations) / time; ms_per_step is the forward +
-adjoint + gradient time.  After the timed region a short seeded request stream (12 requests
-of 64^3 and 128^3 grids by default) runs through the continuous-batching server, and its
-p50 / p99 latency and solves/s go into the line's "serving" object.
+adjoint + gradient time.  After the timed region the same iteration written with cuFFT and
+element-wise torch kernels is timed on the same grid ("cufft_comparison"), and a short
+seeded request stream (12 requests of 64^3 and 128^3 grids by default) runs through the
+continuous-batching server, its p50 / p99 latency and solves/s going into "serving".
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
@@ -161,6 +162,39 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def cufft_comparison(plan, eps, wl, iters, stream):
+    """The same iteration written with cuFFT and element-wise torch kernels
+    (paper_2506_15411_gb300.cufft_reference), timed with CUDA events for `iters` iterations
+    after 3, and both paths run 24 iterations from zero to cross-check the iterate."""
+    import torch
+    from paper_2506_15411_gb300 import PlaneWave
+    from paper_2506_15411_gb300.cufft_reference import TorchCBS
+    k0sq, epsilon = plan.splitting()
+    ref = TorchCBS(eps, PITCH, LAM, 1.0, wl.pad_lo, wl.pad_hi, k0sq, epsilon)
+    nz, ny, nx = eps.shape
+    Et = torch.zeros((3, nz, ny, nx), dtype=torch.complex64, device=eps.device)
+    ref.iterate(Et, 3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ref.iterate(Et, iters)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_iter = e0.elapsed_time(e1) / iters
+    K = 24
+    Et.zero_()
+    ref.iterate(Et, K)
+    plan.set_solver(0.0, K, K)
+    Eo, _ = plan.forward(PlaneWave())
+    torch.cuda.synchronize()
+    diff = float(torch.linalg.vector_norm(Eo - Et) / torch.linalg.vector_norm(Et))
+    del ref, Et, Eo
+    torch.cuda.empty_cache()
+    return {"what": "same iteration with torch.fft (cuFFT) 3D FFTs and element-wise torch kernels",
+            "ms_per_iteration": ms_iter, "iterations_timed": iters,
+            "rel_diff_after_24_iterations": diff}
+
+
 def combine_ranks(times_ms, counts, world, device):
     """Replicas: the slowest rank's time of each timed region (max) and the work of all ranks
     (sum); with one rank, the inputs.  Returns (times, counts) as lists."""
@@ -247,6 +281,9 @@ def run_gpu(args, rank, world, local_rank):
 
     (ms_max, e_ms_max), (iters_all, e_iters_all) = combine_ranks([ms, e_ms], [float(iters), float(e_iters)],
                                                                  world, dev)
+    cufft = None
+    if rank == 0 and args.cufft_iters > 0:
+        cufft = cufft_comparison(plan, eps, wl, args.cufft_iters, stream)
     if rank != 0:
         plan.close()
         return
@@ -287,6 +324,9 @@ def run_gpu(args, rank, world, local_rank):
         from paper_2506_15411_gb300.serve import measure_stream
         serving = measure_stream(args.serve_requests, [_in.parse_size(v) for v in args.serve_sizes],
                                  tol=args.tol)
+    if cufft is not None:
+        cufft["ours_ms_per_iteration"] = iter_ms
+        cufft["speedup_of_fused_kernels"] = cufft["ms_per_iteration"] / iter_ms
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic", "config": cfg,
@@ -297,7 +337,8 @@ def run_gpu(args, rank, world, local_rank):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * N,
                     "d2h_bytes_per_step": 4 * N + 8, "ms_per_step": e_ms_max / args.steps},
-            "gpu_launches": launches * world, "clocks": clocks, "serving": serving}
+            "gpu_launches": launches * world, "clocks": clocks, "serving": serving,
+            "cufft_comparison": cufft}
     print(json.dumps(line), flush=True)
 
 
@@ -344,6 +385,8 @@ def main():
                     help="requests of the served-latency stream after the timed region (0: none; "
                          "skipped when --tol <= 0)")
     ap.add_argument("--serve-sizes", nargs="+", default=["64", "128"], help="grid sizes of that stream")
+    ap.add_argument("--cufft-iters", type=int, default=20,
+                    help="iterations of the cuFFT comparison timed after the timed region (0: none)")
     ap.add_argument("--print-digest", action="store_true", help="print the CUDA source digest and exit")
     args = ap.parse_args()
     if args.print_digest:
