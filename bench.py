@@ -42,6 +42,7 @@ GRID = (275, 275, 315)
 PITCH = LAM / 16
 D_LENS, NA, N_LENS = 16e-6, 0.84, 1.5
 METRIC = "CBS voxel-iters/s"
+ORACLE_ITERS = 2     # oracle iterations of the full grid: CPU baseline and equal-iteration parity
 UNIT = "voxel-iter/s"
 WORKLOAD = "fresnel_lens_275x275x315_lambda16_fwd_adj_grad"
 # algorithmic HBM bytes per voxel of each pass (complex64 fields, 3 components, V complex64)
@@ -124,16 +125,18 @@ class ClockSampler:
                 "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
 
 
-def cpu_oracle_iteration_rate(wl, iters=1):
-    """FP64 oracle, one iteration (after its set-up) on the full grid: voxel-iters/s."""
+def cpu_oracle_iteration_rate(wl, iters=1, want_field=False):
+    """FP64 oracle, `iters` iterations from zero (after its set-up) on the full grid:
+    (voxel-iters/s, seconds, worker threads[, field])."""
     from oracle import cbs_oracle as co
     g = co.Grid(*GRID, PITCH, LAM, 1.0, wl.pad_lo, wl.pad_hi)
     k2 = co.k_squared(g, wl.eps)
     S = co.plane_wave_source(g)
     t = time.perf_counter()
-    co.cbs_solve(g, k2, S, tol=0.0, max_iter=iters)
+    r = co.cbs_solve(g, k2, S, tol=0.0, max_iter=iters)
     dt = time.perf_counter() - t
-    return g.n_vox * iters / dt, dt, co.WORKERS
+    out = (g.n_vox * iters / dt, dt, co.WORKERS)
+    return out + (r.E,) if want_field else out
 
 
 def run_reference(args, rank, world):
@@ -284,6 +287,12 @@ def run_gpu(args, rank, world, local_rank):
     cufft = None
     if rank == 0 and args.cufft_iters > 0:
         cufft = cufft_comparison(plan, eps, wl, args.cufft_iters, stream)
+    E_k = None
+    if rank == 0 and not args.no_cpu_baseline:
+        # the GPU iterate after ORACLE_ITERS iterations from zero, for the oracle comparison
+        plan.set_solver(0.0, ORACLE_ITERS, ORACLE_ITERS)
+        Eg, _ = plan.forward(src)
+        E_k = Eg.cpu().numpy()
     if rank != 0:
         plan.close()
         return
@@ -305,11 +314,16 @@ def run_gpu(args, rank, world, local_rank):
     iter_ms = sum(p["avg_ms"] for p in pass_table.values())
 
     cpu = None
+    parity = None
     if not args.no_cpu_baseline:
-        rate, dt, cores = cpu_oracle_iteration_rate(wl)
+        rate, dt, cores, E_o = cpu_oracle_iteration_rate(wl, ORACLE_ITERS, want_field=True)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"one FP64 oracle iteration of the full {nx}x{ny}x{nz} grid ({dt:.1f} s; "
-                         "scipy.fft workers = cores, NumPy elementwise on one core)"}
+               "sample": f"{ORACLE_ITERS} FP64 oracle iterations from zero of the full {nx}x{ny}x{nz} grid "
+                         f"({dt:.1f} s; scipy.fft workers = cores, NumPy elementwise on one core)"}
+        parity = {"against": "FP64 oracle, equal iteration count from zero", "iterations": ORACLE_ITERS,
+                  "field_rel_l2": float(np.linalg.norm(E_k - E_o) / np.linalg.norm(E_o)),
+                  "field_max_abs_rel": float(np.abs(E_k - E_o).max() / np.abs(E_o).max())}
+        del E_o
     sf, sa, obj = stats[-1]
     cfg = base_config(wl, args.tol)
     cfg.update({"iters_forward": sf.iters, "iters_adjoint": sa.iters, "rel_resid_forward": sf.rel_resid,
@@ -334,7 +348,7 @@ def run_gpu(args, rank, world, local_rank):
                          "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
                          "traffic": traffic,
                          "algorithmic_bytes_per_launch": PASS_BYTES[dom] * N},
-            "cpu_baseline": cpu,
+            "cpu_baseline": cpu, "parity": parity,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * N,
                     "d2h_bytes_per_step": 4 * N + 8, "ms_per_step": e_ms_max / args.steps},
             "gpu_launches": launches * world, "clocks": clocks, "serving": serving,
