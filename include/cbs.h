@@ -301,6 +301,14 @@ int cbs_server_take(cbs_server_t server, cbs_result* out, int max, double timeou
 /* Requests waiting for admission, requests admitted, device bytes held by slots. */
 int cbs_server_info(cbs_server_t server, long long* queued, long long* active, double* bytes_used);
 
+/* Self-test of the failure path of the tile kernels: every wait of theirs on a tensor copy is
+ * bounded and, when it gives up, records an error the host reads after the block of
+ * iterations (CBS_ERR_CUDA, "a tensor-copy wait timed out") instead of hanging the GPU.  This
+ * runs that bounded wait on an mbarrier nothing completes, on the current device, and checks
+ * that it gave up (*device_status = 1) and that the context still takes work.  Returns CBS_OK,
+ * or CBS_ERR_CUDA with a message. */
+int cbs_selftest_wait_timeout(int* device_status);
+
 /* Free the plan and its device memory (NULL is a no-op). */
 void cbs_destroy(cbs_plan_t plan);
 

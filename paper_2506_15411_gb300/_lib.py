@@ -31,7 +31,8 @@ EXPORTS = ("cbs_plan", "cbs_set_permittivity", "cbs_get_splitting", "cbs_set_sol
            "cbs_set_profiling", "cbs_pass_times", "cbs_splitting_noalloc", "cbs_destroy",
            "cbs_last_error", "cbs_design_create", "cbs_design_destroy", "cbs_design_reset",
            "cbs_design_permittivity", "cbs_design_height_gradient", "cbs_design_adam", "cbs_design_step",
-           "cbs_server_create", "cbs_server_destroy", "cbs_server_submit", "cbs_server_take", "cbs_server_info")
+           "cbs_server_create", "cbs_server_destroy", "cbs_server_submit", "cbs_server_take", "cbs_server_info",
+           "cbs_selftest_wait_timeout")
 
 # cbs_pass_times slots: the series' first forward x pass (launched once per series, not
 # timed), then the four kernels of every iteration
@@ -108,6 +109,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "cbs_pass_times": (c_int, [P, POINTER(c_double * 5), POINTER(ctypes.c_longlong * 5), c_int]),
         "cbs_splitting_noalloc": (c_int, [POINTER(cbs_plan_desc), P, POINTER(c_double), POINTER(c_double)]),
         "cbs_destroy": (None, [P]),
+        "cbs_selftest_wait_timeout": (c_int, [POINTER(c_int)]),
         "cbs_server_create": (c_int, [POINTER(c_void_p), POINTER(cbs_server_desc)]),
         "cbs_server_destroy": (None, [P]),
         "cbs_server_submit": (c_int, [P, POINTER(cbs_request), POINTER(ctypes.c_longlong)]),

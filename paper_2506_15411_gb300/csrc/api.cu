@@ -30,6 +30,7 @@
 
 #include "../../include/cbs.h"
 #include "plan.h"
+#include "tma.cuh"
 
 namespace cbs {
 cudaError_t xpass_set_smem_limit(int bytes);
@@ -940,6 +941,29 @@ int cbs_gradient(cbs_plan_t p, const void* E_dev, const void* Eadj_dev, const in
     CK(cudaMemcpyAsync(objective, p->dobj, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
   }
   CK(cudaStreamSynchronize(p->stream));
+  return CBS_OK;
+}
+
+int cbs_selftest_wait_timeout(int* device_status) {
+  g_err.clear();
+  if (!device_status) return fail(CBS_ERR_ARG, "NULL argument");
+  *device_status = 0;
+  int* err = nullptr;
+  cudaStream_t s = nullptr;
+  CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  cudaError_t e = cudaMalloc(&err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = launch_wait_selftest(err, 2000, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(device_status, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  // the context must still take work after the timed-out wait
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (err) cudaFree(err);
+  cudaStreamDestroy(s);
+  if (e != cudaSuccess) return fail(CBS_ERR_CUDA, "self-test: %s", cudaGetErrorString(e));
+  if (*device_status != kErrTmaTimeout)
+    return fail(CBS_ERR_CUDA, "self-test: the bounded wait did not report its timeout (status %d)", *device_status);
   return CBS_OK;
 }
 

@@ -99,6 +99,9 @@ cudaError_t launch_gradient(const float2* E, const float2* Ea, size_t N, float c
 cudaError_t launch_objective(const float2* E, size_t N, int nx, int ny, int x, int y, int z,
                              double* out, cudaStream_t s);
 
+// Bounded-wait self-test (misc.cu): *err = 1 (tensor-copy wait timed out) after `limit` polls.
+cudaError_t launch_wait_selftest(int* err, long long limit, cudaStream_t s);
+
 // Inverse-design kernels on the thickness map (design.cu).
 cudaError_t launch_mirror(const float* in, float* out, int nx, int ny, cudaStream_t s);
 cudaError_t launch_filter(const float* in, float* out, int nx, int ny, const float* w, int R, int axis,

@@ -9,6 +9,7 @@
 #include <cfloat>
 #include <cstdint>
 #include "cbs_internal.h"
+#include "tma.cuh"
 
 namespace cbs {
 
@@ -182,6 +183,24 @@ cudaError_t launch_objective(const float2* E, size_t N, int nx, int ny, int x, i
                              double* out, cudaStream_t s) {
   const size_t idx = ((size_t)z * ny + y) * nx + x;
   k_objective<<<1, 32, 0, s>>>(E, N, idx, out);
+  return cudaGetLastError();
+}
+
+// Self-test of the bounded waits: an mbarrier that nothing arrives at, waited on with the
+// tile kernels' bounded wait (`limit` polls).  The wait must give up, the kernel record the
+// timeout in *err and return -- the error path every tile kernel takes instead of hanging.
+__global__ void k_wait_selftest(int* err, long long limit) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0, limit)) atomicExch(err, kErrTmaTimeout);
+}
+
+cudaError_t launch_wait_selftest(int* err, long long limit, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(err, limit);
   return cudaGetLastError();
 }
 

@@ -12,8 +12,9 @@
 // its result back into the tile from either buffer.
 //
 // Two tile layouts:
-//   columns  element i of column col at base[i * NCOL + col]  (y and z passes; consecutive
-//            threads take consecutive columns)
+//   columns  element i of column col of component c at base[c * cs + i * NCOL + col]  (y and
+//            z passes; a butterfly takes a pair of adjacent columns, consecutive threads take
+//            consecutive pairs)
 //   rows     element i of row `row` of component c at base[c * cs + row * ld + i]  (x passes;
 //            consecutive threads take consecutive butterflies of a row)
 // Divisions by the per-stage counts use float reciprocals (exact for the small integers here).
@@ -24,8 +25,6 @@
 #include <type_traits>
 
 namespace cbs {
-
-constexpr int kMaxRadix = 16;
 
 // Stage q of a plan: {r, Ns, stride = n/r, twstep = n/(Ns r)} and {1/stride, 1/Ns}.
 __device__ __forceinline__ int4 stage_of(const AxisPlan& ap, int q) { return __ldg(&ap.st[2 * q]); }

@@ -101,21 +101,10 @@ __device__ __forceinline__ void bulk_wait_read_1() {
 // Order this thread's generic-proxy shared-memory writes before later async-proxy reads.
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Block set-up of a tile kernel: thread 0 checks that the tile base is 128-byte aligned (as
-// tensor copies require; the tile kernels declare no static shared memory, so the dynamic
-// base is) and initialises the mbarrier; a misaligned tile aborts the block uniformly.
-__device__ __forceinline__ bool block_setup(const void* tile, uint64_t* bar, int* fail, int* err) {
-  if (threadIdx.x == 0) {
-    *fail = (smem_u32(tile) & 127u) ? 1 : 0;
-    if (*fail) atomicExch(err, kErrMisaligned);
-    mbar_init(bar, 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  return *fail == 0;
-}
-
-// Block set-up of a pipelined tile kernel: as block_setup, with `nbar` mbarriers.
+// Block set-up of a pipelined tile kernel: thread 0 checks that the tile base is 128-byte
+// aligned (as tensor copies require; the tile kernels declare no static shared memory, so the
+// dynamic base is) and initialises the `nbar` mbarriers; a misaligned tile aborts the block
+// uniformly.
 __device__ __forceinline__ bool block_setup_n(const void* tile, uint64_t* bars, int nbar, int* fail, int* err) {
   if (threadIdx.x == 0) {
     *fail = (smem_u32(tile) & 127u) ? 1 : 0;
