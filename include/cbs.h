@@ -213,6 +213,17 @@ void cbs_design_destroy(cbs_design_t design);
 /* Zero Adam's moments and step count. */
 int cbs_design_reset(cbs_design_t design);
 
+/* Checkpoint / resume of the design loop.  Its state is the map h (held by the caller),
+ * Adam's first and second moments (float32 [ny][nx] each) and the number of Adam steps
+ * taken, t (the bias corrections use beta^t).  get copies the moments into m / v and writes
+ * t; set loads them, so that the next cbs_design_adam or cbs_design_step on this object does
+ * exactly what it would have done on the object the state came from (same plan shape and
+ * desc).  m and v hold ny*nx floats each and may be device or host memory (any address CUDA
+ * can copy from or to); both calls block until the copies are done.  Errors: CBS_ERR_ARG
+ * (NULL argument, t < 0), CBS_ERR_CUDA. */
+int cbs_design_get_state(cbs_design_t design, float* m, float* v, int* t);
+int cbs_design_set_state(cbs_design_t design, const float* m, const float* v, int t);
+
 /* h -> h_eff (into h_eff_dev when not NULL) -> eps_r (float32 [nz][ny][nx] into eps_dev). */
 int cbs_design_permittivity(cbs_design_t design, const float* h_dev, float* h_eff_dev, float* eps_dev);
 

@@ -30,6 +30,7 @@ EXPORTS = ("cbs_plan", "cbs_set_permittivity", "cbs_get_splitting", "cbs_set_sol
            "cbs_forward", "cbs_adjoint", "cbs_gradient", "cbs_objective", "cbs_design_step_host",
            "cbs_set_profiling", "cbs_pass_times", "cbs_splitting_noalloc", "cbs_destroy",
            "cbs_last_error", "cbs_design_create", "cbs_design_destroy", "cbs_design_reset",
+           "cbs_design_get_state", "cbs_design_set_state",
            "cbs_design_permittivity", "cbs_design_height_gradient", "cbs_design_adam", "cbs_design_step",
            "cbs_server_create", "cbs_server_destroy", "cbs_server_submit", "cbs_server_take", "cbs_server_info",
            "cbs_selftest_wait_timeout")
@@ -118,6 +119,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "cbs_design_create": (c_int, [POINTER(c_void_p), P, POINTER(cbs_design_desc)]),
         "cbs_design_destroy": (None, [P]),
         "cbs_design_reset": (c_int, [P]),
+        "cbs_design_get_state": (c_int, [P, P, P, POINTER(c_int)]),
+        "cbs_design_set_state": (c_int, [P, P, P, c_int]),
         "cbs_design_permittivity": (c_int, [P, P, P, P]),
         "cbs_design_height_gradient": (c_int, [P, P, P, P]),
         "cbs_design_adam": (c_int, [P, P, P]),

@@ -1164,6 +1164,33 @@ int cbs_design_reset(cbs_design_t D) {
   return CBS_OK;
 }
 
+int cbs_design_get_state(cbs_design_t D, float* m, float* v, int* t) {
+  g_err.clear();
+  if (!D || !m || !v || !t) return fail(CBS_ERR_ARG, "NULL argument");
+  int rc = sync_in(D->p);
+  if (rc) return rc;
+  const size_t mb = (size_t)D->nx * D->ny * sizeof(float);
+  CK(cudaMemcpyAsync(m, D->m, mb, cudaMemcpyDefault, D->p->stream));
+  CK(cudaMemcpyAsync(v, D->v, mb, cudaMemcpyDefault, D->p->stream));
+  CK(cudaStreamSynchronize(D->p->stream));
+  *t = D->t;
+  return CBS_OK;
+}
+
+int cbs_design_set_state(cbs_design_t D, const float* m, const float* v, int t) {
+  g_err.clear();
+  if (!D || !m || !v) return fail(CBS_ERR_ARG, "NULL argument");
+  if (t < 0) return fail(CBS_ERR_ARG, "step count %d < 0", t);
+  int rc = sync_in(D->p);
+  if (rc) return rc;
+  const size_t mb = (size_t)D->nx * D->ny * sizeof(float);
+  CK(cudaMemcpyAsync(D->m, m, mb, cudaMemcpyDefault, D->p->stream));
+  CK(cudaMemcpyAsync(D->v, v, mb, cudaMemcpyDefault, D->p->stream));
+  CK(cudaStreamSynchronize(D->p->stream));
+  D->t = t;
+  return CBS_OK;
+}
+
 int cbs_design_permittivity(cbs_design_t D, const float* h_dev, float* h_eff_dev, float* eps_dev) {
   g_err.clear();
   if (!D || !h_dev || !eps_dev) return fail(CBS_ERR_ARG, "NULL argument");

@@ -37,6 +37,9 @@ class Design:
                  beta2: float = 0.999, adam_eps: float = 1e-6):
         self.plan = plan
         self.lib = plan.lib
+        self.params = dict(z_base=int(z_base), n_lens=float(n_lens), aperture_um=float(aperture_um),
+                           h_max_um=float(h_max_um), sigma_um=float(sigma_um), mirror=bool(mirror),
+                           alpha=float(alpha), beta1=float(beta1), beta2=float(beta2), adam_eps=float(adam_eps))
         d = L.cbs_design_desc(int(z_base), float(n_lens), float(aperture_um), float(h_max_um), float(sigma_um),
                               1 if mirror else 0, float(alpha), float(beta1), float(beta2), float(adam_eps))
         h = ctypes.c_void_p()
@@ -70,6 +73,52 @@ class Design:
 
     def reset(self):
         L.check(self.lib.cbs_design_reset(self.handle))
+
+    def state_dict(self, h: torch.Tensor, fields: bool = False) -> dict:
+        """The loop's state for a checkpoint: the map h, Adam's moments m and v, the step
+        count t, the design parameters and the plan's grid; with fields=True also the last
+        forward and adjoint fields, so that a warm-started next step resumes exactly."""
+        self._check_map(h, "h")
+        m = torch.empty(self.map_shape, dtype=torch.float32, device=self.plan.device)
+        v = torch.empty_like(m)
+        t = ctypes.c_int()
+        L.check(self.lib.cbs_design_get_state(self.handle, ctypes.c_void_p(_ptr(m)), ctypes.c_void_p(_ptr(v)),
+                                              ctypes.byref(t)))
+        state = {"h": h.detach().clone(), "m": m, "v": v, "t": t.value, "params": dict(self.params),
+                 "grid": tuple(self.plan.shape)}
+        if fields and self.E is not None:
+            state["E"] = self.E.clone()
+            state["E_adj"] = self.E_adj.clone()
+        return state
+
+    def load_state_dict(self, state: dict) -> torch.Tensor:
+        """Restore a state_dict() into this object (same grid and parameters) and return the
+        map h on the plan's device; the next step continues as the saved loop would have."""
+        if tuple(state["grid"]) != tuple(self.plan.shape) or state["params"] != self.params:
+            raise ValueError("checkpoint is of another grid or design parameters")
+        dev = self.plan.device
+        h = state["h"].to(device=dev, dtype=torch.float32).contiguous()
+        m = state["m"].to(device=dev, dtype=torch.float32).contiguous()
+        v = state["v"].to(device=dev, dtype=torch.float32).contiguous()
+        for name, x in (("h", h), ("m", m), ("v", v)):
+            self._check_map(x, name)
+        L.check(self.lib.cbs_design_set_state(self.handle, ctypes.c_void_p(_ptr(m)), ctypes.c_void_p(_ptr(v)),
+                                              int(state["t"])))
+        if "E" in state:
+            self.E = state["E"].to(dev).contiguous()
+            self.E_adj = state["E_adj"].to(dev).contiguous()
+        else:
+            self.E = self.E_adj = None
+        return h
+
+    def save(self, path: str, h: torch.Tensor, fields: bool = False):
+        """Write state_dict(h, fields) to path (torch.save, tensors moved to the host)."""
+        st = self.state_dict(h, fields)
+        torch.save({k: (x.cpu() if isinstance(x, torch.Tensor) else x) for k, x in st.items()}, path)
+
+    def load(self, path: str) -> torch.Tensor:
+        """Restore a checkpoint written by save(); returns h on the plan's device."""
+        return self.load_state_dict(torch.load(path, map_location="cpu", weights_only=True))
 
     def permittivity(self, h: torch.Tensor):
         """(eps_r float32 (nz, ny, nx), h_eff float32 (ny, nx)) of the map h."""
@@ -156,7 +205,8 @@ def main():
         python -m paper_2506_15411_gb300.design --grid 256 256 192 --ppl 8 --pads 8 8 24 \\
             --D-um 25 --steps 5
 
-    prints one JSON line per step (objective, iterations, seconds)."""
+    prints one JSON line per step (objective, iterations, seconds).  --checkpoint PATH saves
+    h, Adam's state and the fields after every step; --resume PATH continues from one."""
     import argparse
     import json
     import math
@@ -181,6 +231,8 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--max-iter", type=int, default=200000)
     ap.add_argument("--warm", type=int, default=2)
+    ap.add_argument("--checkpoint", default=None, help="write the loop's state here after every step")
+    ap.add_argument("--resume", default=None, help="start from a checkpoint written by --checkpoint")
     args = ap.parse_args()
     nx, ny, nz = args.grid
     lam = args.lam_nm * 1e-9
@@ -200,9 +252,13 @@ def main():
                  max_iter=args.max_iter, check_every=64) as plan:
         with Design(plan, z_base, args.n_lens, args.D_um, h_max, args.sigma_um) as d:
             h = torch.from_numpy(h0).to(plan.device)
+            if args.resume:
+                h = d.load(args.resume)
             for k in range(args.steps):
                 t0 = time.perf_counter()
-                info = d.step(h, PlaneWave(), r0, warm_start=args.warm if k > 0 else 0)
+                info = d.step(h, PlaneWave(), r0, warm_start=args.warm if k > 0 or args.resume else 0)
+                if args.checkpoint:
+                    d.save(args.checkpoint, h, fields=True)
                 torch.cuda.synchronize()
                 print(json.dumps({"step": k, "objective": info.objective, "fwd_iters": info.fwd.iters,
                                   "adj_iters": info.adj.iters, "fwd_status": info.fwd.status,

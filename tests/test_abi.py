@@ -90,3 +90,12 @@ def test_return_codes_match_header():
                  "CBS_ERR_CUDA", "CBS_ERR_STATE", "CBS_ERR_STAGNATED", "CBS_SRC_PLANE_WAVE", "CBS_SRC_POINT", "CBS_SRC_USER"):
         m = re.search(r"#define\s+%s\s+\(?(-?\d+)\)?" % name, text)
         assert m and int(m.group(1)) == getattr(L, name), name
+
+
+def test_design_state_calls_reject_null_arguments(built_lib):
+    """The checkpoint entry points check their arguments before touching the device."""
+    lib = L.load(built_lib)
+    t = ctypes.c_int(7)
+    assert lib.cbs_design_get_state(None, None, None, ctypes.byref(t)) == L.CBS_ERR_ARG
+    assert b"NULL" in lib.cbs_last_error() and t.value == 7
+    assert lib.cbs_design_set_state(None, None, None, 0) == L.CBS_ERR_ARG
