@@ -233,6 +233,9 @@ def main():
     ap.add_argument("--warm", type=int, default=2)
     ap.add_argument("--checkpoint", default=None, help="write the loop's state here after every step")
     ap.add_argument("--resume", default=None, help="start from a checkpoint written by --checkpoint")
+    ap.add_argument("--check-every", type=int, default=64)
+    ap.add_argument("--pass-times", action="store_true",
+                    help="time the solver's passes with CUDA events and print their averages at the end")
     args = ap.parse_args()
     nx, ny, nz = args.grid
     lam = args.lam_nm * 1e-9
@@ -249,7 +252,9 @@ def main():
         raise SystemExit(f"focus z = {zf} falls in the absorbing layer")
     r0 = (nx // 2, ny // 2, zf)
     with CBSPlan(nx, ny, nz, pitch, lam, 1.0, tuple(args.pads), tuple(args.pads), tol=args.tol,
-                 max_iter=args.max_iter, check_every=64) as plan:
+                 max_iter=args.max_iter, check_every=args.check_every) as plan:
+        if args.pass_times:
+            plan.set_profiling(True)
         with Design(plan, z_base, args.n_lens, args.D_um, h_max, args.sigma_um) as d:
             h = torch.from_numpy(h0).to(plan.device)
             if args.resume:
@@ -263,9 +268,15 @@ def main():
                 print(json.dumps({"step": k, "objective": info.objective, "fwd_iters": info.fwd.iters,
                                   "adj_iters": info.adj.iters, "fwd_status": info.fwd.status,
                                   "adj_status": info.adj.status, "seconds": time.perf_counter() - t0,
+                                  "solve_seconds": info.seconds,
+                                  "ms_per_iter": 1e3 * info.seconds / max(1, info.fwd.iters + info.adj.iters),
                                   "grid": [nx, ny, nz], "pitch_nm": pitch * 1e9}), flush=True)
                 if not math.isfinite(info.objective):
                     raise SystemExit("non-finite objective")
+        if args.pass_times:
+            t = plan.pass_times()
+            print(json.dumps({"pass_avg_ms": {k: v[0] / max(1, v[1]) for k, v in t.items()},
+                              "timed_launches": {k: v[1] for k, v in t.items()}}), flush=True)
 
 
 if __name__ == "__main__":
