@@ -40,6 +40,15 @@ the paper leaves open is marked READING.
 
 Array layout: fields are complex128 arrays of shape (3, nz, ny, nx) (component order x, y,
 z; x fastest in memory), scalar grids are (nz, ny, nx).
+
+What pins what (tests/test_oracle_pins.py, test_mie.py): the fixed point against a dense
+solve of the discrete system and the homogeneous closed form; the physics scale and time
+convention against the closed-form dyadic Green function and Mie scattering; the adjoint
+against reciprocity; the gradient against central differences.  Parity unpinned by the
+paper: the layer profile and its strength (layer_strength, axis_profile, absorption), the
+plane-wave sheet's placement (plane_wave_source) and the stopping rule are READINGS; each
+is pinned only to its own stated definition (the 1e-4 round trip, the unit plane wave in a
+homogeneous medium), not to a number the paper prints.
 """
 from __future__ import annotations
 

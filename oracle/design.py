@@ -20,6 +20,10 @@ Readings where the paper is silent:
   * Adam (Kingma & Ba, Algorithm 1) on the loss -L with h and alpha in micrometres,
     bias-corrected moments; afterwards h is clamped to [0, h_max] and set to 0 outside
     the aperture r <= D/2 (there the moments are not updated).
+Parity unpinned by the paper: these readings (units, subpixel rule, mirror average, filter
+radius, constraints) are pinned to their own definitions (scipy's Gaussian filter, torch's
+Adam, central differences of dense solves; tests/test_oracle_design.py), not to a number the
+paper prints.
 """
 from __future__ import annotations
 
