@@ -49,6 +49,8 @@ extern "C" {
 #define CBS_ERR_STAGNATED (-7)      /* tol > 0 not reached and the residual stopped falling
                                        (no new 1 % minimum over max(1000, it/4) iterations):
                                        the FP32 rounding floor; E holds the last iterate */
+#define CBS_ERR_TIME_LIMIT (-8)     /* the solve's wall-clock limit (cbs_set_time_limit) ran
+                                       out before tol was reached; E holds the last iterate */
 
 typedef struct cbs_plan_s* cbs_plan_t;
 
@@ -113,10 +115,16 @@ int cbs_get_splitting(cbs_plan_t plan, double* k0sq, double* epsilon);
 /* Change the stopping rule of later solves (same meaning as in cbs_plan_desc). */
 int cbs_set_solver(cbs_plan_t plan, double tol, int max_iter, int check_every);
 
+/* Wall-clock limit of later solves, in seconds from the solve's start (0: none, the default).
+ * It is checked on the host after each block of check_every iterations, so a solve may run
+ * up to one block past it; it then ends with CBS_ERR_TIME_LIMIT and E holds the last
+ * iterate.  Errors: CBS_ERR_ARG (NULL plan, negative or non-finite seconds). */
+int cbs_set_time_limit(cbs_plan_t plan, double seconds);
+
 /* Forward solve: iterate the series for source *src into E_dev (complex64 [3][nz][ny][nx]).
  * Returns CBS_OK, CBS_ERR_NOT_CONVERGED (tol > 0 not reached in max_iter; E_dev holds the
- * last iterate), CBS_ERR_STAGNATED (residual at its FP32 floor above tol), CBS_ERR_DIVERGED,
- * CBS_ERR_ARG, CBS_ERR_STATE or CBS_ERR_CUDA. */
+ * last iterate), CBS_ERR_STAGNATED (residual at its FP32 floor above tol),
+ * CBS_ERR_TIME_LIMIT, CBS_ERR_DIVERGED, CBS_ERR_ARG, CBS_ERR_STATE or CBS_ERR_CUDA. */
 int cbs_forward(cbs_plan_t plan, const cbs_source* src, void* E_dev, cbs_stats* stats);
 
 /* Adjoint solve for the figure of merit |E(r0)|^2: E_adj = A^{-1}[conj(E(r0)) delta_r0],
@@ -240,8 +248,8 @@ int cbs_design_adam(cbs_design_t design, float* h_dev, const float* grad_h_dev);
  * E_dev and the adjoint solve of |E(r0)|^2 into Eadj_dev (both warm-started from their
  * contents when src->warm_start is 1 or 2, with that meaning), the gradient, dL/dh (copied
  * into grad_h_dev when not NULL) and the Adam update of h_dev in place.  *objective =
- * |E(r0)|^2 before the update.  fwd/adj may be NULL.  A solve that ends NOT_CONVERGED or
- * STAGNATED does not stop the step (its status is in fwd/adj); other errors return at the
+ * |E(r0)|^2 before the update.  fwd/adj may be NULL.  A solve that ends NOT_CONVERGED,
+ * STAGNATED or TIME_LIMIT does not stop the step (its status is in fwd/adj); other errors return at the
  * failing step, with h_dev not updated. */
 int cbs_design_step(cbs_design_t design, float* h_dev, const cbs_source* src, const int r0[3],
                     void* E_dev, void* Eadj_dev, float* grad_h_dev, double* objective,

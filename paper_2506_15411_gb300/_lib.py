@@ -20,6 +20,9 @@ CBS_ERR_DIVERGED = -4
 CBS_ERR_CUDA = -5
 CBS_ERR_STATE = -6
 CBS_ERR_STAGNATED = -7
+CBS_ERR_TIME_LIMIT = -8
+# solves that end with the last iterate in E and raise nothing in the binding
+NONFATAL = (CBS_OK, CBS_ERR_NOT_CONVERGED, CBS_ERR_STAGNATED, CBS_ERR_TIME_LIMIT)
 
 CBS_SRC_PLANE_WAVE = 0
 CBS_SRC_POINT = 1
@@ -28,7 +31,7 @@ CBS_SRC_USER = 2
 # Every symbol include/cbs.h declares.
 EXPORTS = ("cbs_plan", "cbs_set_permittivity", "cbs_get_splitting", "cbs_set_solver",
            "cbs_forward", "cbs_adjoint", "cbs_gradient", "cbs_objective", "cbs_design_step_host",
-           "cbs_set_profiling", "cbs_pass_times", "cbs_splitting_noalloc", "cbs_destroy",
+           "cbs_set_profiling", "cbs_pass_times", "cbs_set_time_limit", "cbs_splitting_noalloc", "cbs_destroy",
            "cbs_last_error", "cbs_design_create", "cbs_design_destroy", "cbs_design_reset",
            "cbs_design_get_state", "cbs_design_set_state",
            "cbs_design_permittivity", "cbs_design_height_gradient", "cbs_design_adam", "cbs_design_step",
@@ -100,6 +103,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "cbs_set_permittivity": (c_int, [P, P]),
         "cbs_get_splitting": (c_int, [P, POINTER(c_double), POINTER(c_double)]),
         "cbs_set_solver": (c_int, [P, c_double, c_int, c_int]),
+        "cbs_set_time_limit": (c_int, [P, c_double]),
         "cbs_forward": (c_int, [P, POINTER(cbs_source), P, POINTER(cbs_stats)]),
         "cbs_adjoint": (c_int, [P, POINTER(c_int * 3), P, P, POINTER(cbs_stats)]),
         "cbs_gradient": (c_int, [P, P, P, POINTER(c_int * 3), P, POINTER(c_double)]),

@@ -53,8 +53,9 @@ def focal_intensity(eps: torch.Tensor, plan: CBSPlan, source, r0,
     E_init warm-starts the forward series (the fixed point does not depend on it), with the
     residual measured against a start from zero, so a close guess stops early.  After
     the call, plan.last_forward / plan.last_field hold the forward Stats and field, and after
-    backward plan.last_adjoint the adjoint Stats; a solve that ends NOT_CONVERGED or
-    STAGNATED does not raise, so callers that need convergence check those Stats."""
+    backward plan.last_adjoint the adjoint Stats; a solve that ends NOT_CONVERGED,
+    STAGNATED or TIME_LIMIT does not raise, so callers that need convergence check those
+    Stats."""
     return FocalIntensity.apply(eps, plan, source, r0, E_init)
 
 

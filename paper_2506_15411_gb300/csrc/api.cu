@@ -319,6 +319,7 @@ size_t field_rows(const cbs_plan_s* p) { return (size_t)3 * p->d.ny * p->d.nz; }
 // and the event the host waits on.
 int series_enqueue_block(cbs_plan_s* p, SeriesRun& R) {
   R.m = std::min(p->d.check_every, p->d.max_iter - R.it);
+  R.blk_range = nvtxRangeStartA("cbs: block of iterations");
   // full blocks replay a graph; with profiling the last iteration runs outside it
   const int ng = (R.m == p->d.check_every) ? (p->profiling ? R.m - 1 : R.m) : 0;
   bool used = false;
@@ -337,6 +338,8 @@ int series_enqueue_block(cbs_plan_s* p, SeriesRun& R) {
 // Sets R.rc on an error and returns whether iterating is over.
 bool series_absorb_block(cbs_plan_s* p, SeriesRun& R) {
   R.iterating = false;
+  nvtxRangeEnd(R.blk_range);
+  R.blk_range = 0;
   if (*p->err_host) {
     R.rc = fail(CBS_ERR_CUDA, "a tensor-copy wait timed out in an FFT pass (device error %d)", *p->err_host);
     return true;
@@ -360,6 +363,14 @@ bool series_absorb_block(cbs_plan_s* p, SeriesRun& R) {
   // converged when the residual at the check (the block's last iteration) is within tol; a
   // dip below tol earlier in the block does not count (the residual is not monotone)
   const bool done = p->d.tol > 0 && R.rel <= p->d.tol;
+  if (!done && p->time_limit_s > 0 && R.it < p->d.max_iter) {
+    const double t = std::chrono::duration<double>(std::chrono::steady_clock::now() - R.t0).count();
+    if (t >= p->time_limit_s) {
+      R.rc = fail(CBS_ERR_TIME_LIMIT, "wall-clock limit %g s reached after %d iterations (relative residual %g)",
+                  p->time_limit_s, R.it, R.rel);
+      return true;
+    }
+  }
   // stagnation: the residual has sat at its rounding floor for a long stretch
   if (!done && p->d.tol > 0 && R.it - R.best_it >= std::max(1000, R.it / 4)) {
     R.rc = fail(CBS_ERR_STAGNATED, "residual stagnated at %g (best %g) after %d iterations, above tol %g", R.rel,
@@ -846,7 +857,16 @@ int cbs_set_solver(cbs_plan_t p, double tol, int max_iter, int check_every) {
   return CBS_OK;
 }
 
+int cbs_set_time_limit(cbs_plan_t p, double seconds) {
+  g_err.clear();
+  if (!p) return fail(CBS_ERR_ARG, "NULL plan");
+  if (!(seconds >= 0) || !std::isfinite(seconds)) return fail(CBS_ERR_ARG, "time limit %g s", seconds);
+  p->time_limit_s = seconds;
+  return CBS_OK;
+}
+
 int cbs_set_permittivity(cbs_plan_t p, const float* eps) {
+  NvtxRange nv("cbs_set_permittivity");
   g_err.clear();
   if (!p || !eps) return fail(CBS_ERR_ARG, "NULL argument");
   int rc = sync_in(p);
@@ -899,6 +919,7 @@ int cbs_get_splitting(cbs_plan_t p, double* k0sq, double* epsilon) {
 }
 
 int cbs_forward(cbs_plan_t p, const cbs_source* src, void* E_dev, cbs_stats* stats) {
+  NvtxRange nv("cbs_forward");
   g_err.clear();
   if (stats) *stats = cbs_stats{};
   if (!p || !src || !E_dev) {
@@ -920,12 +941,14 @@ int cbs_forward(cbs_plan_t p, const cbs_source* src, void* E_dev, cbs_stats* sta
 }
 
 int cbs_adjoint(cbs_plan_t p, const int r0[3], const void* E_dev, void* Eadj_dev, cbs_stats* stats) {
+  NvtxRange nv("cbs_adjoint");
   g_err.clear();
   return adjoint_run(p, r0, E_dev, Eadj_dev, 0, stats);
 }
 
 int cbs_gradient(cbs_plan_t p, const void* E_dev, const void* Eadj_dev, const int r0[3], float* grad_dev,
                  double* objective) {
+  NvtxRange nv("cbs_gradient");
   g_err.clear();
   if (!p || !E_dev || !Eadj_dev || !grad_dev) return fail(CBS_ERR_ARG, "NULL argument");
   int rc = sync_in(p);
@@ -1228,6 +1251,7 @@ int cbs_design_adam(cbs_design_t D, float* h_dev, const float* grad_h_dev) {
 
 int cbs_design_step(cbs_design_t D, float* h_dev, const cbs_source* src, const int r0[3], void* E_dev,
                     void* Eadj_dev, float* grad_h_dev, double* objective, cbs_stats* fwd, cbs_stats* adj) {
+  NvtxRange nv("cbs_design_step");
   g_err.clear();
   if (fwd) *fwd = cbs_stats{};
   if (adj) *adj = cbs_stats{};
@@ -1246,10 +1270,10 @@ int cbs_design_step(cbs_design_t D, float* h_dev, const cbs_source* src, const i
   cbs_stats f{}, a{};
   rc = run_series(p, static_cast<float2*>(E_dev), s, src->warm_start, &f);
   if (fwd) *fwd = f;
-  if (rc && rc != CBS_ERR_NOT_CONVERGED && rc != CBS_ERR_STAGNATED) return rc;
+  if (!nonfatal(rc)) return rc;
   rc = adjoint_run(p, r0, E_dev, Eadj_dev, src->warm_start, &a);
   if (adj) *adj = a;
-  if (rc && rc != CBS_ERR_NOT_CONVERGED && rc != CBS_ERR_STAGNATED) return rc;
+  if (!nonfatal(rc)) return rc;
   const float coef = (float)(2.0 * p->kvac * p->kvac);
   CK(launch_gradient(static_cast<const float2*>(E_dev), static_cast<const float2*>(Eadj_dev), p->N, coef, D->grad,
                      p->stream));

@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <chrono>
 #include <vector>
@@ -25,6 +26,20 @@ int fail(int code, const char* fmt, ...);
   } while (0)
 
 namespace cbs {
+
+// An NVTX range over a scope (host timeline of the API calls, for nsys and `ncu --nvtx`);
+// without a tool attached the calls do nothing.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// Solves that return with the last iterate in E and do not stop a design step or a request.
+inline bool nonfatal(int rc) {
+  return rc == CBS_OK || rc == CBS_ERR_NOT_CONVERGED || rc == CBS_ERR_STAGNATED || rc == CBS_ERR_TIME_LIMIT;
+}
 
 // A captured block of iterations bakes in the field pointer and the whole source.
 struct GraphEntry {
@@ -81,6 +96,7 @@ struct cbs_plan_s {
   // graphs of one block of check_every iterations, per (E, source) binding
   std::vector<cbs::GraphEntry> graphs;
   // pass timing (events around the launches of the last iteration of each block)
+  double time_limit_s = 0;         // wall-clock limit of a solve (0: none)
   bool profiling = false;
   cudaEvent_t pev[6] = {};
   double pass_ms[5] = {};
@@ -101,6 +117,7 @@ struct SeriesRun {
   bool iterating = false;  // a block is in flight (blk_ev marks its residuals on the host)
   bool copying = false;    // the copy-out is in flight (blk_ev marks its end)
   bool finished = false;
+  nvtxRangeId_t blk_range = 0;   // NVTX range of the block in flight
   std::chrono::steady_clock::time_point t0;
 };
 

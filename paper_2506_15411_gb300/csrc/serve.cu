@@ -122,7 +122,7 @@ struct cbs_server_s {
 
 namespace {
 
-bool fatal(int rc) { return rc != CBS_OK && rc != CBS_ERR_NOT_CONVERGED && rc != CBS_ERR_STAGNATED; }
+bool fatal(int rc) { return !nonfatal(rc); }
 
 void finish(cbs_server_s* S, Slot* s, int status) {
   s->res.status = status;

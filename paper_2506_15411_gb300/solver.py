@@ -130,6 +130,11 @@ class CBSPlan:
     def set_profiling(self, on: bool):
         L.check(self.lib.cbs_set_profiling(self.handle, 1 if on else 0))
 
+    def set_time_limit(self, seconds: float):
+        """Wall-clock limit of later solves (0: none); checked after each block of
+        check_every iterations, a solve past it ends with status CBS_ERR_TIME_LIMIT."""
+        L.check(self.lib.cbs_set_time_limit(self.handle, float(seconds)))
+
     def pass_times(self, reset: bool = False):
         """{pass name: (summed ms, timed launches)} since the last reset."""
         ms = (ctypes.c_double * 5)()
@@ -168,7 +173,8 @@ class CBSPlan:
         """Solve for the field of `source`; returns (E, Stats).  warm_start: 0 starts from
         zero; 1 from E with residuals relative to this run's first; 2 from E with residuals
         relative to a start from zero (stops early for a close guess).  Raises on errors
-        other than 'not converged' and 'stagnated' (then Stats.status says which)."""
+        other than 'not converged', 'stagnated' and 'time limit' (then Stats.status says
+        which)."""
         if E is None:
             if warm_start:
                 raise ValueError("warm_start needs E")
@@ -177,7 +183,7 @@ class CBSPlan:
         s = self._source(source, int(warm_start))
         st = L.cbs_stats()
         L.check(self.lib.cbs_forward(self.handle, ctypes.byref(s), ctypes.c_void_p(_ptr(E)),
-                                     ctypes.byref(st)), allow=(L.CBS_OK, L.CBS_ERR_NOT_CONVERGED, L.CBS_ERR_STAGNATED))
+                                     ctypes.byref(st)), allow=L.NONFATAL)
         return E, _stats(st)
 
     def adjoint(self, r0, E: torch.Tensor, E_adj: Optional[torch.Tensor] = None):
@@ -190,7 +196,7 @@ class CBSPlan:
         st = L.cbs_stats()
         L.check(self.lib.cbs_adjoint(self.handle, ctypes.byref(r), ctypes.c_void_p(_ptr(E)),
                                      ctypes.c_void_p(_ptr(E_adj)), ctypes.byref(st)),
-                allow=(L.CBS_OK, L.CBS_ERR_NOT_CONVERGED, L.CBS_ERR_STAGNATED))
+                allow=L.NONFATAL)
         return E_adj, _stats(st)
 
     def gradient(self, E: torch.Tensor, E_adj: torch.Tensor, r0=None, grad: Optional[torch.Tensor] = None):

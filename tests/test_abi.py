@@ -87,7 +87,7 @@ int main(void) {
 def test_return_codes_match_header():
     text = open(HEADER).read()
     for name in ("CBS_OK", "CBS_ERR_ARG", "CBS_ERR_OOM", "CBS_ERR_NOT_CONVERGED", "CBS_ERR_DIVERGED",
-                 "CBS_ERR_CUDA", "CBS_ERR_STATE", "CBS_ERR_STAGNATED", "CBS_SRC_PLANE_WAVE", "CBS_SRC_POINT", "CBS_SRC_USER"):
+                 "CBS_ERR_CUDA", "CBS_ERR_STATE", "CBS_ERR_STAGNATED", "CBS_ERR_TIME_LIMIT", "CBS_SRC_PLANE_WAVE", "CBS_SRC_POINT", "CBS_SRC_USER"):
         m = re.search(r"#define\s+%s\s+\(?(-?\d+)\)?" % name, text)
         assert m and int(m.group(1)) == getattr(L, name), name
 
@@ -99,3 +99,9 @@ def test_design_state_calls_reject_null_arguments(built_lib):
     assert lib.cbs_design_get_state(None, None, None, ctypes.byref(t)) == L.CBS_ERR_ARG
     assert b"NULL" in lib.cbs_last_error() and t.value == 7
     assert lib.cbs_design_set_state(None, None, None, 0) == L.CBS_ERR_ARG
+
+
+def test_time_limit_rejects_a_null_plan(built_lib):
+    lib = L.load(built_lib)
+    assert lib.cbs_set_time_limit(None, 1.0) == L.CBS_ERR_ARG
+    assert b"NULL" in lib.cbs_last_error()

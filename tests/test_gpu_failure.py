@@ -28,3 +28,34 @@ def test_bounded_wait_times_out_and_the_context_stays_usable():
         E, s = plan.forward(PlaneWave())
         torch.cuda.synchronize()
     assert s.iters == 8 and np.isfinite(E.abs().max().item())
+
+
+def test_wall_clock_limit_ends_a_solve_with_its_last_iterate():
+    """A limit that runs out stops the series at a block boundary with CBS_ERR_TIME_LIMIT and
+    the last iterate in E (equal to a plain run of the same number of iterations); a limit
+    that does not run out leaves the result unchanged."""
+    import torch
+    from paper_2506_15411_gb300 import CBSPlan, PlaneWave
+    from paper_2506_15411_gb300 import _lib as L
+    n = 64
+    eps = torch.from_numpy(inputs.random_eps(n, n, n, seed=4)).cuda()
+    with CBSPlan(n, n, n, LAM / 8, LAM, 1.0, (8,) * 3, (8,) * 3, tol=1e-12, max_iter=1_000_000,
+                 check_every=16) as plan:
+        plan.set_permittivity(eps)
+        plan.set_time_limit(0.05)
+        E, s = plan.forward(PlaneWave())
+        torch.cuda.synchronize()
+        assert s.status == L.CBS_ERR_TIME_LIMIT and not s.converged
+        assert 16 <= s.iters < 1_000_000 and s.iters % 16 == 0 and 0.05 <= s.seconds < 5.0
+        assert np.isfinite(E.abs().max().item())
+        plan.set_time_limit(0.0)
+        plan.set_solver(0.0, s.iters, 16)
+        E2, s2 = plan.forward(PlaneWave())
+        plan.set_time_limit(600.0)
+        E3, s3 = plan.forward(PlaneWave())
+        torch.cuda.synchronize()
+    assert s2.status == L.CBS_OK and s2.iters == s.iters and torch.equal(E, E2)
+    assert s3.status == L.CBS_OK and s3.iters == s.iters and torch.equal(E2, E3)
+    with pytest.raises(L.CBSError):
+        with CBSPlan(n, n, n, LAM / 8, LAM, 1.0, (8,) * 3, (8,) * 3) as plan:
+            plan.set_time_limit(-1.0)
