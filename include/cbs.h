@@ -57,7 +57,11 @@ typedef struct cbs_plan_s* cbs_plan_t;
 /* Problem and solver description (copied by cbs_plan). */
 typedef struct {
   int nx, ny, nz;         /* grid, including the absorbing layers; each a product of
-                             2, 3, 5, 7, 11, 13 and at most 1024 */
+                             2, 3, 5, 7, 11, 13 and at most 1024.  nz is further bounded by
+                             the z tiles (whole z columns of 3 components, double-buffered,
+                             in shared memory): every such nz <= 714 is supported, longer
+                             ones (up to 756) only where the tensor-copy boxes divide nz;
+                             cbs_plan returns CBS_ERR_ARG for the others */
   double pitch_m;         /* voxel pitch [m] (isotropic) */
   double lambda_m;        /* vacuum wavelength [m] */
   double n_bg;            /* background index; sets the layer strength */

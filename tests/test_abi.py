@@ -105,3 +105,26 @@ def test_time_limit_rejects_a_null_plan(built_lib):
     lib = L.load(built_lib)
     assert lib.cbs_set_time_limit(None, 1.0) == L.CBS_ERR_ARG
     assert b"NULL" in lib.cbs_last_error()
+
+
+def test_plan_rejects_bad_descriptions_before_touching_the_device(built_lib):
+    """Sizes outside [1, 1024], lengths with a prime factor above 13, layers that do not fit,
+    non-positive physics and solver settings: CBS_ERR_ARG, *out = NULL, no CUDA call."""
+    lib = L.load(built_lib)
+    lam = 1.064e-6
+
+    def plan(nx=16, ny=16, nz=16, pitch=lam / 8, lo=(2, 2, 2), hi=(2, 2, 2), n_bg=1.0, max_iter=10, check_every=8):
+        d = L.cbs_plan_desc(nx, ny, nz, pitch, lam, n_bg, (ctypes.c_int * 3)(*lo), (ctypes.c_int * 3)(*hi),
+                            1e-4, max_iter, check_every, None)
+        h = ctypes.c_void_p(1)
+        rc = lib.cbs_plan(ctypes.byref(h), ctypes.byref(d))
+        return rc, h.value, lib.cbs_last_error().decode()
+
+    for kw, words in [(dict(nx=0), "outside"), (dict(ny=1025), "outside"), (dict(nz=-3), "outside"),
+                      (dict(nx=17), "product"), (dict(nz=34), "product"), (dict(lo=(9, 2, 2)), "pads"),
+                      (dict(hi=(2, 2, -1)), "pads"), (dict(lo=(8, 2, 2), hi=(8, 2, 2)), "pads"),
+                      (dict(pitch=0.0), "positive"), (dict(n_bg=-1.0), "positive"),
+                      (dict(max_iter=0), ">= 1"), (dict(check_every=0), ">= 1")]:
+        rc, h, msg = plan(**kw)
+        assert rc == L.CBS_ERR_ARG and h is None and words in msg, (kw, rc, msg)
+    assert lib.cbs_plan(None, None) == L.CBS_ERR_ARG
