@@ -1,16 +1,23 @@
 #!/usr/bin/env python
-"""Benchmark of the GB300 CBS solver: CBS voxel-iterations per second.
+"""Benchmark of the GB300 CBS solver: CBS voxel-iterations per second at paper scale.
 
-One step is one design iteration of the paper's method on the Fresnel-lens workload
-(D = 16 um, NA 0.84, lambda = 1064 nm, n = 1.5 on n = 1.0, 275 x 275 x 315 voxels at
-lambda/16 with absorbing layers [lambda, lambda, 6 lambda] = [16, 16, 96] voxels per face):
-set the permittivity (potential and splitting), forward solve of the x-polarised plane wave
-to the relative residual --tol, adjoint solve for the focal intensity |E(r0)|^2, gradient.
-The metric is voxels x (forward + adjoint iterations) / time; ms_per_step is the forward +
-adjoint + gradient time.  After the timed region the same iteration written with cuFFT and
-element-wise torch kernels is timed on the same grid ("cufft_comparison"), and a short
-seeded request stream (12 requests of 64^3 and 128^3 grids by default) runs through the
-continuous-batching server, its p50 / p99 latency and solves/s going into "serving".
+One step is one design iteration of the paper's method on the design volume of Fig. 4:
+621 x 621 x 261 voxels at 177 nm (lambda = 1064 nm) plus absorbing layers
+[lambda, lambda, 6 lambda] = [6, 6, 36] voxels per face, padded to the FFT lengths
+640 x 640 x 336 (137.6 M voxels), holding the D = 109 um, NA 0.84, n = 1.54 Fresnel lens the
+design starts from: set the permittivity (potential and splitting), a forward solve of the
+x-polarised plane wave and an adjoint solve of the focal intensity |E(r0)|^2 of --iters
+iterations each, and the gradient.  A converged solve on this volume takes of the order of
+1e4 iterations; a fixed count keeps a step at the cost of a design iteration's solves and
+makes the work per step exact.  The metric is voxels x (forward + adjoint iterations) / time.
+
+After the timed region:
+  * "parity": the GPU's forward field, adjoint field and gradient after 2 iterations from zero
+    against the FP64 CPU oracle on the full grid (the same legs time "cpu_baseline");
+  * "fresnel_lens_275x275x315": one converged design iteration (relative residual --tol) of
+    the Fig. 1 lens workload (D = 16 um, NA 0.84, n = 1.5, 275 x 275 x 315 at lambda/16);
+  * "cufft_comparison": the same iteration written with cuFFT and element-wise torch kernels;
+  * "serving": a short seeded request stream through the continuous-batching server.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
@@ -38,32 +45,48 @@ sys.path.insert(0, ROOT)
 from paper_2506_15411_gb300 import inputs  # noqa: E402
 
 LAM = 1.064e-6
-GRID = (275, 275, 315)
-PITCH = LAM / 16
-D_LENS, NA, N_LENS = 16e-6, 0.84, 1.5
+# headline workload: the paper-scale design volume (Fig. 4)
+GRID = (640, 640, 336)
+PITCH = 177e-9
+PADS = (6, 6, 36)
+D_LENS, NA, N_LENS = 109e-6, 0.84, 1.54
+ITERS = 200
+WORKLOAD = "paper_scale_lens_640x640x336_177nm_fwd200_adj200_grad"
+# secondary workload: the Fig. 1 lens, solved to a relative residual
+C2_GRID = (275, 275, 315)
+C2_PITCH = LAM / 16
+C2_LENS = (16e-6, 0.84, 1.5)
+C2_WORKLOAD = "fresnel_lens_275x275x315_lambda16_fwd_adj_grad"
+
 METRIC = "CBS voxel-iters/s"
-ORACLE_ITERS = 2     # oracle iterations of the full grid: CPU baseline and equal-iteration parity
 UNIT = "voxel-iter/s"
-WORKLOAD = "fresnel_lens_275x275x315_lambda16_fwd_adj_grad"
+ORACLE_ITERS = 2     # oracle iterations per solve: CPU baseline and equal-iteration parity
 # algorithmic HBM bytes per voxel of each pass (complex64 fields, 3 components, V complex64)
 # (k_xpass_fwd runs once per solve; every iteration runs the other four: 248 B per voxel)
 PASS_BYTES = {"k_xpass_fwd": 56, "k_ypass_fwd": 48, "k_zpass_green": 48, "k_ypass_inv": 48,
               "k_xpass_inv_fwd": 104}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_paper_scale_640x640x336.json")
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
 
 def workload():
-    return inputs.fresnel_lens_workload(*GRID, PITCH, LAM, D_LENS, NA, N_LENS)
+    return inputs.fresnel_lens_workload(*GRID, PITCH, LAM, D_LENS, NA, N_LENS, pad_lo=PADS, pad_hi=PADS)
 
 
-def base_config(wl, tol):
+def c2_workload():
+    return inputs.fresnel_lens_workload(*C2_GRID, C2_PITCH, LAM, *C2_LENS)
+
+
+def base_config(wl, iters):
     nx, ny, nz = GRID
     return {"workload": WORKLOAD, "grid_xyz": list(GRID), "voxels": nx * ny * nz,
-            "pitch_nm": round(PITCH * 1e9, 3), "lambda_nm": LAM * 1e9, "pads_per_face_xyz": list(wl.pad_lo),
+            "design_volume_xyz": [621, 621, 261],
+            "pitch_nm": round(PITCH * 1e9, 3), "lambda_nm": LAM * 1e9, "pads_per_face_xyz": list(PADS),
             "lens": {"D_um": D_LENS * 1e6, "NA": NA, "n": N_LENS}, "focus_voxel_xyz": list(wl.r0),
-            "tol": tol, "l2": "inputs larger than L2 (E, E_adj, W: 572 MB each; V 191 MB)"}
+            "iters_per_solve": iters,
+            "l2": "inputs larger than L2 (E, E_adj, W: 3.3 GB each; V 1.1 GB)"}
 
 
 def peaks():
@@ -73,6 +96,38 @@ def peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def host_memory_gb():
+    """Memory this process may still use on the host (MemAvailable, capped by a cgroup limit)."""
+    avail = None
+    try:
+        for ln in open("/proc/meminfo"):
+            if ln.startswith("MemAvailable:"):
+                avail = int(ln.split()[1]) * 1024
+    except Exception:
+        pass
+    for path in ("/sys/fs/cgroup/memory.max", "/sys/fs/cgroup/memory/memory.limit_in_bytes"):
+        try:
+            v = open(path).read().strip()
+            if v.isdigit():
+                lim = int(v)
+                used = 0
+                for up in ("/sys/fs/cgroup/memory.current", "/sys/fs/cgroup/memory/memory.usage_in_bytes"):
+                    try:
+                        used = int(open(up).read().strip())
+                        break
+                    except Exception:
+                        pass
+                avail = lim - used if avail is None else min(avail, lim - used)
+        except Exception:
+            pass
+    return None if avail is None else avail / 1e9
+
+
+# peak host memory of the oracle legs on the full grid (FP64 fields of 6.6 GB, FFT work
+# arrays and the GPU fields brought back for the comparison), in GB
+ORACLE_HOST_GB = 110.0
 
 
 class ClockSampler:
@@ -125,42 +180,69 @@ class ClockSampler:
                 "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
 
 
-def cpu_oracle_iteration_rate(wl, iters=1, want_field=False):
-    """FP64 oracle, `iters` iterations from zero (after its set-up) on the full grid:
-    (voxel-iters/s, seconds, worker threads[, field])."""
+def parity_voxel(wl):
+    """Objective voxel of the equal-iteration oracle comparison: on the axis, one voxel past
+    the plane-wave sheet.  Two iterations build the field up only within a few voxels of the
+    sheet (after two iterations the field falls by about 3x per voxel away from it with this
+    grid's shift epsilon = 9.6 k_vac^2), so the focus itself still holds rounding noise."""
+    return (GRID[0] // 2, GRID[1] // 2, wl.z_source + 1)
+
+
+def oracle_design_iteration(wl, iters, r0):
+    """FP64 oracle on the full grid: `iters` forward iterations from zero, `iters` adjoint
+    iterations of |E(r0)|^2 from zero, the gradient.  Returns a dict with the fields, the
+    solve time (set-up excluded) and the worker threads."""
     from oracle import cbs_oracle as co
     g = co.Grid(*GRID, PITCH, LAM, 1.0, wl.pad_lo, wl.pad_hi)
     k2 = co.k_squared(g, wl.eps)
     S = co.plane_wave_source(g)
+    sp = co.splitting(k2)
     t = time.perf_counter()
-    r = co.cbs_solve(g, k2, S, tol=0.0, max_iter=iters)
+    fwd = co.cbs_solve(g, k2, S, tol=0.0, max_iter=iters, split=sp)
+    del S
+    Sa = co.adjoint_source(g, fwd.E, r0)
+    adj = co.cbs_solve(g, k2, Sa, tol=0.0, max_iter=iters, split=sp)
     dt = time.perf_counter() - t
-    out = (g.n_vox * iters / dt, dt, co.WORKERS)
-    return out + (r.E,) if want_field else out
+    del Sa, k2
+    grad = co.gradient(g, fwd.E, adj.E)
+    return {"E": fwd.E, "Ea": adj.E, "grad": grad, "objective": co.objective(fwd.E, r0),
+            "seconds": dt, "iters": 2 * iters, "workers": co.WORKERS, "split": sp}
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the FP64 CPU oracle as it stands, one iteration per step."""
+    """Reference arm: the FP64 CPU oracle as it stands, one iteration of the full grid per
+    step (set-up once, before the warm-up)."""
     if rank != 0:
         return
+    from oracle import cbs_oracle as co
     wl = workload()
     N = int(np.prod(GRID))
-    for _ in range(args.warmup):
-        cpu_oracle_iteration_rate(wl)
+    g = co.Grid(*GRID, PITCH, LAM, 1.0, wl.pad_lo, wl.pad_hi)
+    k2 = co.k_squared(g, wl.eps)
+    S = co.plane_wave_source(g)
+    sp = co.splitting(k2)
+    E = None
     times = []
-    cores = 1
-    for _ in range(args.steps):
-        _, dt, cores = cpu_oracle_iteration_rate(wl)
-        times.append(dt)
+    for i in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        r = co.cbs_solve(g, k2, S, tol=0.0, max_iter=1, E0=E, split=sp)
+        dt = time.perf_counter() - t
+        E = r.E
+        if i >= args.warmup:
+            times.append(dt)
     total = sum(times)
     value = N * args.steps / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-            "data": "synthetic", "config": dict(base_config(wl, args.tol), parallelism="host cores"),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "one FP64 oracle iteration of the full 275x275x315 grid per step "
-                                       "(scipy.fft workers = cores, NumPy elementwise on one core)"},
+            "data": "synthetic", "config": dict(base_config(wl, args.iters), parallelism="host cores"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": co.WORKERS, "kind": "oracle",
+                             "sample": f"one FP64 oracle iteration of the full {GRID[0]}x{GRID[1]}x{GRID[2]} "
+                                       "grid per step (scipy.fft workers = cores, NumPy elementwise on one core)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -168,7 +250,7 @@ def run_reference(args, rank, world):
 def cufft_comparison(plan, eps, wl, iters, stream):
     """The same iteration written with cuFFT and element-wise torch kernels
     (paper_2506_15411_gb300.cufft_reference), timed with CUDA events for `iters` iterations
-    after 3, and both paths run 24 iterations from zero to cross-check the iterate."""
+    after 3, and both paths run 8 iterations from zero to cross-check the iterate."""
     import torch
     from paper_2506_15411_gb300 import PlaneWave
     from paper_2506_15411_gb300.cufft_reference import TorchCBS
@@ -184,7 +266,7 @@ def cufft_comparison(plan, eps, wl, iters, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     ms_iter = e0.elapsed_time(e1) / iters
-    K = 24
+    K = 8
     Et.zero_()
     ref.iterate(Et, K)
     plan.set_solver(0.0, K, K)
@@ -195,7 +277,7 @@ def cufft_comparison(plan, eps, wl, iters, stream):
     torch.cuda.empty_cache()
     return {"what": "same iteration with torch.fft (cuFFT) 3D FFTs and element-wise torch kernels",
             "ms_per_iteration": ms_iter, "iterations_timed": iters,
-            "rel_diff_after_24_iterations": diff}
+            f"rel_diff_after_{K}_iterations": diff}
 
 
 def combine_ranks(times_ms, counts, world, device):
@@ -209,6 +291,54 @@ def combine_ranks(times_ms, counts, world, device):
         dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
         dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
     return tmax.tolist(), tsum.tolist()
+
+
+def pass_table(passes, N):
+    passes = {k: v for k, v in passes.items() if v[1] > 0}   # the per-iteration kernels
+    tot = sum(v[0] for v in passes.values())
+    return {k: {"avg_ms": v[0] / v[1], "timed_launches": v[1], "share": v[0] / tot,
+                "bytes_per_voxel": PASS_BYTES[k],
+                "GBps_algorithmic": PASS_BYTES[k] * N / (v[0] / v[1] / 1e3) / 1e9}
+            for k, v in passes.items()}
+
+
+def secondary_c2(args, stream, dev):
+    """One converged design iteration of the Fig. 1 lens (set eps, forward and adjoint to
+    relative residual args.tol, gradient), after one untimed one."""
+    import torch
+    from paper_2506_15411_gb300 import CBSPlan, PlaneWave
+    wl = c2_workload()
+    nx, ny, nz = C2_GRID
+    N = nx * ny * nz
+    eps = torch.from_numpy(wl.eps).to(dev)
+    E = torch.empty((3, nz, ny, nx), dtype=torch.complex64, device=dev)
+    Ea = torch.empty_like(E)
+    grad = torch.empty((nz, ny, nx), dtype=torch.float32, device=dev)
+    with CBSPlan(nx, ny, nz, C2_PITCH, LAM, 1.0, wl.pad_lo, wl.pad_hi, tol=args.tol, max_iter=args.max_iter,
+                 check_every=64, device=dev, stream=stream) as plan:
+        def step():
+            plan.set_permittivity(eps)
+            _, sf = plan.forward(PlaneWave(), E=E)
+            _, sa = plan.adjoint(wl.r0, E, Ea)
+            _, obj = plan.gradient(E, Ea, wl.r0, grad)
+            return sf, sa, obj
+        step()
+        plan.set_profiling(True)
+        plan.pass_times(reset=True)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sf, sa, obj = step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        table = pass_table(plan.pass_times(reset=True), N)
+    it = sf.iters + sa.iters
+    return {"workload": C2_WORKLOAD, "grid_xyz": list(C2_GRID), "pads_per_face_xyz": list(wl.pad_lo),
+            "tol": args.tol, "ms_fwd_adj_grad": ms, "iters_forward": sf.iters, "iters_adjoint": sa.iters,
+            "rel_resid_forward": sf.rel_resid, "rel_resid_adjoint": sa.rel_resid, "objective": obj,
+            "voxel_iters_per_s": N * it / (ms / 1e3),
+            "iteration_ms": sum(p["avg_ms"] for p in table.values()), "passes": table}
 
 
 def run_gpu(args, rank, world, local_rank):
@@ -227,8 +357,9 @@ def run_gpu(args, rank, world, local_rank):
     E = torch.empty((3, nz, ny, nx), dtype=torch.complex64, device=dev)
     Ea = torch.empty_like(E)
     grad = torch.empty((nz, ny, nx), dtype=torch.float32, device=dev)
-    plan = CBSPlan(nx, ny, nz, PITCH, LAM, 1.0, wl.pad_lo, wl.pad_hi, tol=args.tol,
-                   max_iter=args.max_iter, check_every=args.check_every, device=dev, stream=stream)
+    check = max(1, args.iters // 2)
+    plan = CBSPlan(nx, ny, nz, PITCH, LAM, 1.0, wl.pad_lo, wl.pad_hi, tol=0.0,
+                   max_iter=args.iters, check_every=check, device=dev, stream=stream)
     src = PlaneWave()
 
     def step():
@@ -284,15 +415,6 @@ def run_gpu(args, rank, world, local_rank):
 
     (ms_max, e_ms_max), (iters_all, e_iters_all) = combine_ranks([ms, e_ms], [float(iters), float(e_iters)],
                                                                  world, dev)
-    cufft = None
-    if rank == 0 and args.cufft_iters > 0:
-        cufft = cufft_comparison(plan, eps, wl, args.cufft_iters, stream)
-    E_k = None
-    if rank == 0 and not args.no_cpu_baseline:
-        # the GPU iterate after ORACLE_ITERS iterations from zero, for the oracle comparison
-        plan.set_solver(0.0, ORACLE_ITERS, ORACLE_ITERS)
-        Eg, _ = plan.forward(src)
-        E_k = Eg.cpu().numpy()
     if rank != 0:
         plan.close()
         return
@@ -301,46 +423,71 @@ def run_gpu(args, rank, world, local_rank):
 
     # roofline of the dominant pass (largest share of timed pass time)
     peak, peak_kind = peaks()
-    passes = {k: v for k, v in passes.items() if v[1] > 0}   # the per-iteration kernels
-    tot = {k: v[0] for k, v in passes.items()}
-    dom = max(tot, key=tot.get)
-    avg_ms = passes[dom][0] / passes[dom][1]
+    table = pass_table(passes, N)
+    dom = max(table, key=lambda k: table[k]["share"])
+    avg_ms = table[dom]["avg_ms"]
     achieved = PASS_BYTES[dom] * N / (avg_ms / 1e3) / 1e9
-    traffic = load_traffic(dom)
-    pass_table = {k: {"avg_ms": v[0] / v[1], "timed_launches": v[1], "share": tot[k] / sum(tot.values()),
-                      "bytes_per_voxel": PASS_BYTES[k],
-                      "GBps_algorithmic": PASS_BYTES[k] * N / (v[0] / v[1] / 1e3) / 1e9}
-                  for k, v in passes.items()}
-    iter_ms = sum(p["avg_ms"] for p in pass_table.values())
+    iter_ms = sum(p["avg_ms"] for p in table.values())
+    sf, sa, obj = stats[-1]
+    cfg = base_config(wl, args.iters)
+    cfg.update({"iters_forward": sf.iters, "iters_adjoint": sa.iters, "rel_resid_forward": sf.rel_resid,
+                "rel_resid_adjoint": sa.rel_resid, "objective": obj, "parallelism": f"replicas x{world}",
+                "iteration_ms": iter_ms, "iteration_GBps_248B": 248 * N / (iter_ms / 1e3) / 1e9,
+                "iteration_frac_248B": 248 * N / (iter_ms / 1e3) / 1e9 / peak,
+                "iteration_frac_280B_model": 280 * N / (iter_ms / 1e3) / 1e9 / peak,
+                "passes": table, "check_every": check})
 
+    # --- after the timed region: oracle parity and CPU baseline ------------------------------
     cpu = None
     parity = None
     if not args.no_cpu_baseline:
-        rate, dt, cores, E_o = cpu_oracle_iteration_rate(wl, ORACLE_ITERS, want_field=True)
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{ORACLE_ITERS} FP64 oracle iterations from zero of the full {nx}x{ny}x{nz} grid "
-                         f"({dt:.1f} s; scipy.fft workers = cores, NumPy elementwise on one core)"}
-        parity = {"against": "FP64 oracle, equal iteration count from zero", "iterations": ORACLE_ITERS,
-                  "field_rel_l2": float(np.linalg.norm(E_k - E_o) / np.linalg.norm(E_o)),
-                  "field_max_abs_rel": float(np.abs(E_k - E_o).max() / np.abs(E_o).max())}
-        del E_o
-    sf, sa, obj = stats[-1]
-    cfg = base_config(wl, args.tol)
-    cfg.update({"iters_forward": sf.iters, "iters_adjoint": sa.iters, "rel_resid_forward": sf.rel_resid,
-                "rel_resid_adjoint": sa.rel_resid, "objective": obj, "parallelism": f"replicas x{world}",
-                "iteration_ms": iter_ms, "passes": pass_table, "check_every": args.check_every})
-    plan.close()
-    serving = None
-    if args.serve_requests > 0 and args.tol > 0:
-        # served-solve latency (the metric's third part), after the timed region: a seeded
-        # stream of small grids through the continuous-batching server
-        from paper_2506_15411_gb300 import inputs as _in
-        from paper_2506_15411_gb300.serve import measure_stream
-        serving = measure_stream(args.serve_requests, [_in.parse_size(v) for v in args.serve_sizes],
-                                 tol=args.tol)
-    if cufft is not None:
+        mem = host_memory_gb()
+        if mem is not None and mem < ORACLE_HOST_GB:
+            parity = {"skipped": f"host memory available {mem:.0f} GB < {ORACLE_HOST_GB:.0f} GB the FP64 "
+                                 "oracle of the full grid needs"}
+        else:
+            rp = parity_voxel(wl)
+            plan.set_permittivity(eps)
+            plan.set_solver(0.0, ORACLE_ITERS, ORACLE_ITERS)
+            Eg, _ = plan.forward(src)
+            Eag, _ = plan.adjoint(rp, Eg)
+            gg, objg = plan.gradient(Eg, Eag, rp)
+            torch.cuda.synchronize(dev)
+            Eg_h, Eag_h, gg_h = Eg.cpu().numpy(), Eag.cpu().numpy(), gg.cpu().numpy()
+            del Eg, Eag, gg
+            o = oracle_design_iteration(wl, ORACLE_ITERS, rp)
+            rate = N * o["iters"] / o["seconds"]
+            cpu = {"value": rate, "unit": UNIT, "cores": o["workers"], "kind": "oracle",
+                   "sample": f"{ORACLE_ITERS} forward + {ORACLE_ITERS} adjoint FP64 oracle iterations from zero "
+                             f"of the full {nx}x{ny}x{nz} grid ({o['seconds']:.1f} s; scipy.fft workers = cores, "
+                             "NumPy elementwise on one core)"}
+            k0g, epg = plan.splitting()
+            parity = {"against": "FP64 oracle, equal iteration count from zero, full grid",
+                      "iterations_per_solve": ORACLE_ITERS, "objective_voxel_xyz": list(rp),
+                      "field_rel_l2": rel_l2(Eg_h, o["E"]),
+                      "adjoint_field_rel_l2": rel_l2(Eag_h, o["Ea"]),
+                      "gradient_rel_l2": rel_l2(gg_h, o["grad"]),
+                      "objective_rel": abs(objg - o["objective"]) / abs(o["objective"]),
+                      "splitting_rel": [abs(k0g - o["split"].k0sq) / abs(o["split"].k0sq),
+                                        abs(epg - o["split"].epsilon) / o["split"].epsilon]}
+            del o, Eg_h, Eag_h, gg_h
+    cufft = None
+    if args.cufft_iters > 0:
+        cufft = cufft_comparison(plan, eps, wl, args.cufft_iters, stream)
         cufft["ours_ms_per_iteration"] = iter_ms
         cufft["speedup_of_fused_kernels"] = cufft["ms_per_iteration"] / iter_ms
+    plan.close()
+    del E, Ea, grad, eps
+    torch.cuda.empty_cache()
+    c2 = secondary_c2(args, stream, dev) if args.c2 and args.tol > 0 else None
+    serving = None
+    if args.serve_requests > 0 and args.tol > 0:
+        # served-solve latency (the metric's third part): a seeded stream of small grids
+        # through the continuous-batching server
+        from paper_2506_15411_gb300.serve import measure_stream
+        serving = measure_stream(args.serve_requests, [inputs.parse_size(v) for v in args.serve_sizes],
+                                 tol=args.tol)
+    traffic = load_traffic(dom)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic", "config": cfg,
@@ -351,8 +498,8 @@ def run_gpu(args, rank, world, local_rank):
             "cpu_baseline": cpu, "parity": parity,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * N,
                     "d2h_bytes_per_step": 4 * N + 8, "ms_per_step": e_ms_max / args.steps},
-            "gpu_launches": launches * world, "clocks": clocks, "serving": serving,
-            "cufft_comparison": cufft}
+            "gpu_launches": launches * world, "clocks": clocks,
+            "fresnel_lens_275x275x315": c2, "serving": serving, "cufft_comparison": cufft}
     print(json.dumps(line), flush=True)
 
 
@@ -369,11 +516,9 @@ def source_digest():
     return h.hexdigest()
 
 
-def load_traffic(kernel):
-    """DRAM bytes per launch of `kernel` on this workload from the committed ncu summary
-    (profiles/traffic_fresnel_lens_275x275x315.json), or None when the kernels have changed
-    since those counters were taken."""
-    path = os.path.join(ROOT, "profiles", "traffic_fresnel_lens_275x275x315.json")
+def load_traffic(kernel, path=TRAFFIC_FILE):
+    """DRAM bytes per launch of `kernel` on the headline workload from the committed ncu
+    summary, or None when the kernels have changed since those counters were taken."""
     try:
         with open(path) as f:
             d = json.load(f)
@@ -388,13 +533,15 @@ def load_traffic(kernel):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--tol", type=float, default=1e-4)
+    ap.add_argument("--iters", type=int, default=ITERS, help="iterations of each solve of a step")
+    ap.add_argument("--tol", type=float, default=1e-4, help="relative residual of the converged lens leg")
     ap.add_argument("--max-iter", type=int, default=200000)
-    ap.add_argument("--check-every", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-c2", dest="c2", action="store_false",
+                    help="skip the converged 275x275x315 lens design iteration")
     ap.add_argument("--serve-requests", type=int, default=12,
                     help="requests of the served-latency stream after the timed region (0: none; "
                          "skipped when --tol <= 0)")

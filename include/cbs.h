@@ -44,7 +44,10 @@ extern "C" {
 #define CBS_ERR_OOM (-2)            /* device allocation failed */
 #define CBS_ERR_NOT_CONVERGED (-3)  /* tol > 0 and max_iter reached; E holds the last iterate */
 #define CBS_ERR_DIVERGED (-4)       /* residual non-finite or grew 1e4-fold; E is garbage */
-#define CBS_ERR_CUDA (-5)           /* a CUDA runtime call failed */
+#define CBS_ERR_CUDA (-5)           /* a CUDA runtime call failed, or a kernel's bounded wait on
+                                       a tensor copy timed out ("a tensor-copy wait timed
+                                       out"): that solve's E is garbage, the plan stays usable
+                                       and the next solve starts from a cleared error flag */
 #define CBS_ERR_STATE (-6)          /* call out of order, e.g. no permittivity set yet */
 #define CBS_ERR_STAGNATED (-7)      /* tol > 0 not reached and the residual stopped falling
                                        (no new 1 % minimum over max(1000, it/4) iterations):
@@ -100,10 +103,13 @@ typedef struct {
   int status;        /* return code of the call */
 } cbs_stats;
 
-/* Create a plan: checks the description, factors each axis into FFT radices and allocates
- * the plan's device memory (potential V: 8 B/voxel; k-space workspace W: 24 B/voxel;
- * twiddles and reduction scratch).  *out receives the plan.  Errors: CBS_ERR_ARG,
- * CBS_ERR_OOM, CBS_ERR_CUDA. */
+/* Create a plan for one problem as the paper states it: a voxel grid of the given pitch,
+ * the vacuum wavelength and absorbing layers of given thickness on every face (thickness
+ * [lambda, lambda, 6 lambda] in the Fig. 1 benchmark paragraph; the 621 x 621 x 261-voxel
+ * design volume at 177 nm of the Fig. 4 paragraph).  Checks the description, factors each
+ * axis into FFT radices and allocates the plan's device memory (potential V: 8 B/voxel;
+ * k-space workspace W and the iterate: 24 B/voxel each; twiddles and reduction scratch).
+ * *out receives the plan.  Errors: CBS_ERR_ARG, CBS_ERR_OOM, CBS_ERR_CUDA. */
 int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc);
 
 /* Set the relative permittivity (real, float32 [nz][ny][nx], layers included; the plan
@@ -125,20 +131,26 @@ int cbs_set_solver(cbs_plan_t plan, double tol, int max_iter, int check_every);
  * iterate.  Errors: CBS_ERR_ARG (NULL plan, negative or non-finite seconds). */
 int cbs_set_time_limit(cbs_plan_t plan, double seconds);
 
-/* Forward solve: iterate the series for source *src into E_dev (complex64 [3][nz][ny][nx]).
+/* Forward solve (the CBS solve of the Fig. 1 benchmark paragraph: the total field of a lens
+ * under a normally incident x-polarised plane wave, Fig. 2 paragraph): iterate the series
+ * for source *src into E_dev (complex64 [3][nz][ny][nx]).
  * Returns CBS_OK, CBS_ERR_NOT_CONVERGED (tol > 0 not reached in max_iter; E_dev holds the
  * last iterate), CBS_ERR_STAGNATED (residual at its FP32 floor above tol),
  * CBS_ERR_TIME_LIMIT, CBS_ERR_DIVERGED, CBS_ERR_ARG, CBS_ERR_STATE or CBS_ERR_CUDA. */
 int cbs_forward(cbs_plan_t plan, const cbs_source* src, void* E_dev, cbs_stats* stats);
 
-/* Adjoint solve for the figure of merit |E(r0)|^2: E_adj = A^{-1}[conj(E(r0)) delta_r0],
+/* Adjoint solve for the figure of merit |E(r0)|^2 (the adjoint field of the figure-of-merit
+ * paragraph): E_adj = A^{-1}[conj(E(r0)) delta_r0],
  * the same series with a raw point source conj(E(r0)) read from E_dev on the device
  * (A = curl curl - k^2 is complex symmetric).  r0 = (x, y, z) voxel.  Eadj_dev starts at 0.
  * Return codes as cbs_forward. */
 int cbs_adjoint(cbs_plan_t plan, const int r0[3], const void* E_dev, void* Eadj_dev,
                 cbs_stats* stats);
 
-/* Gradient dL/d eps_r(r) = 2 k_vac^2 Re[E_adj(r) . E(r)] into grad_dev (float32
+/* Gradient of the figure of merit L = |E(r0)|^2 (Fig. 2 caption) from the forward and the
+ * adjoint field (the 3D gradient of the figure-of-merit paragraph, there taken with respect to
+ * the shape S(r); per unit of permittivity here):
+ * dL/d eps_r(r) = 2 k_vac^2 Re[E_adj(r) . E(r)] into grad_dev (float32
  * [nz][ny][nx]); when r0 and objective are not NULL also *objective = |E(r0)|^2 (FP64).
  * Errors: CBS_ERR_ARG, CBS_ERR_CUDA. */
 int cbs_gradient(cbs_plan_t plan, const void* E_dev, const void* Eadj_dev, const int r0[3],
@@ -180,11 +192,14 @@ int cbs_pass_times(cbs_plan_t plan, double ms_total[5], long long launches[5], i
  *   eps_real_dev: float32 [nz][ny][nx] on the current device, layers included.
  * Scratch: one ~80 KB array in device memory per device that loads the library, kept until
  * the process exits.  The first call on a device looks up its address (do that first call
- * before any stream capture).  Every call shares the array and leaves its contents behind;
+ * before any stream capture) and keeps it for the life of the process: after a
+ * cudaDeviceReset of that device the kept address is stale, so do not call this entry point
+ * again on a device that has been reset.  Every call shares the array and leaves its contents behind;
  * calls that overlap on the GPU (other streams or threads) race and give wrong results.
  * Limit: nx * ny * nz <= 268,435,456 voxels (4096 blocks of 65,536); larger grids return
- * CBS_ERR_ARG.  Other errors: CBS_ERR_ARG (NULL, bad dims or pads, non-finite eps,
- * epsilon = 0), CBS_ERR_CUDA.  Blocks the host until the result is back. */
+ * CBS_ERR_ARG.  Other errors: CBS_ERR_ARG (NULL; dims or pads that cbs_plan rejects:
+ * an axis outside [1, 1024], a pad over half its axis; non-finite eps; epsilon = 0),
+ * CBS_ERR_CUDA.  Blocks the host until the result is back. */
 int cbs_splitting_noalloc(const cbs_plan_desc* desc, const float* eps_real_dev, double* k0sq,
                           double* epsilon);
 

@@ -411,8 +411,12 @@ void series_begin(cbs_plan_s* p, float2* E, const SourceArgs& src, int warm, Ser
   R.a = p->base;
   R.a.E = p->Ei;   // iterate on the plan's padded copy; the caller's E is read and written once
   R.a.src = src;
+  // every run starts from a clean error flag and residual counter: a run that a timed-out
+  // tensor-copy wait ended left both behind, and everything else it touched (W, the
+  // iterate, the partial sums) is recomputed from the plan's inputs below
   cudaError_t e = cudaMemsetAsync(p->Ei, 0, 3 * R.a.Nw * sizeof(float2), p->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->counter, 0, sizeof(unsigned), p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->err_dev, 0, sizeof(int), p->stream);
   if (e != cudaSuccess) {
     R.rc = fail(CBS_ERR_CUDA, "field set-up: %s", cudaGetErrorString(e));
     R.finished = true;

@@ -32,6 +32,7 @@ constexpr int kMaxBlocks = 4096;                 // partial sums held in the scr
 constexpr long long kVoxelsPerBlock = 65536;     // each block reduces one chunk of the grid
 constexpr int kThreads = 256;
 constexpr int kMaxDevices = 64;
+constexpr int kMaxAxis = 1024;                   // longest axis cbs_plan accepts
 
 struct Scratch {
   float pmin[kMaxBlocks];
@@ -156,7 +157,9 @@ __global__ void k_noalloc_maxdev(const float* __restrict__ eps, long long N, Lay
   }
 }
 
-// Device address of g_scratch, looked up once per device with that device current.
+// Device address of g_scratch, looked up once per device with that device current (the
+// primary context's copy of the array; a cudaDeviceReset ends that context, and the cached
+// address with it -- the header says so).
 std::mutex g_mu;
 Scratch* g_ptr[kMaxDevices] = {};
 
@@ -189,10 +192,13 @@ extern "C" int cbs_splitting_noalloc(const cbs_plan_desc* d, const float* eps_re
                                      double* epsilon) {
   cbs::set_last_error("");
   if (!d || !eps_real_dev || !k0sq || !epsilon) return err(CBS_ERR_ARG, "NULL argument");
+  // the descriptor checks of cbs_plan, so that both entry points accept the same grids
   const int dims[3] = {d->nx, d->ny, d->nz};
   for (int a = 0; a < 3; ++a) {
-    if (dims[a] < 1) return err(CBS_ERR_ARG, "axis %d size %d < 1", a, dims[a]);
-    if (d->pad_lo[a] < 0 || d->pad_hi[a] < 0 || d->pad_lo[a] + d->pad_hi[a] >= dims[a])
+    if (dims[a] < 1 || dims[a] > kMaxAxis)
+      return err(CBS_ERR_ARG, "axis %d size %d outside [1, %d]", a, dims[a], kMaxAxis);
+    if (d->pad_lo[a] < 0 || d->pad_hi[a] < 0 || 2 * d->pad_lo[a] > dims[a] || 2 * d->pad_hi[a] > dims[a] ||
+        d->pad_lo[a] + d->pad_hi[a] >= dims[a])
       return err(CBS_ERR_ARG, "axis %d pads (%d, %d) do not fit size %d", a, d->pad_lo[a], d->pad_hi[a], dims[a]);
   }
   if (!(d->pitch_m > 0) || !(d->lambda_m > 0) || !(d->n_bg > 0))

@@ -69,7 +69,13 @@ struct Job {
   long long id = 0;
   cbs_request r{};
   double t_submit = 0;
+  int passed = 0;          // later requests admitted while this one did not fit
 };
+
+// A queued request that does not fit yet lets later ones pass at most this many times; then
+// nothing behind it is admitted until it fits (memory frees as running requests finish), so
+// a large request in a stream of small ones waits a bounded time.
+constexpr int kMaxPassed = 8;
 
 enum class Phase { Idle, Forward, Adjoint, Output };
 
@@ -110,7 +116,8 @@ struct cbs_server_s {
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Job> incoming;              // submitted, not yet seen by the worker
-  std::deque<Job> queue;                 // waiting for admission (worker only)
+  std::list<Job> queue;                  // waiting for admission (worker only; a list, so
+                                         // erasing one keeps pointers to the others valid)
   std::deque<cbs_result> done;           // completed, not yet taken
   long long next_id = 1;
   bool stop = false;
@@ -268,11 +275,14 @@ bool advance(cbs_server_s* S, Slot* s) {
   return false;
 }
 
-// Admit queued requests in arrival order while the limits allow (a request that does not fit
-// yet lets later, smaller ones pass).  Returns whether anything was admitted.
+// Admit queued requests in arrival order while the limits allow.  A request that does not fit
+// yet lets later ones pass, kMaxPassed times at most; after that admission waits for it.
+// Returns whether anything was admitted.
 bool admit(cbs_server_s* S) {
   bool any = false;
+  Job* blocked = nullptr;   // the oldest queued request that did not fit in this pass
   for (auto it = S->queue.begin(); it != S->queue.end();) {
+    if (blocked && blocked->passed >= kMaxPassed) break;
     long long active;
     {
       std::lock_guard<std::mutex> lk(S->mu);
@@ -319,6 +329,7 @@ bool admit(cbs_server_s* S) {
           any = true;
           continue;
         }
+        if (!blocked) blocked = &*it;
         ++it;
         continue;
       }
@@ -343,6 +354,7 @@ bool admit(cbs_server_s* S) {
       S->slots.push_back(slot);
       S->bytes_used += slot->bytes;
     }
+    if (blocked) blocked->passed += 1;
     slot->job = *it;
     slot->res = cbs_result{};
     slot->res.id = it->id;

@@ -59,3 +59,27 @@ def test_wall_clock_limit_ends_a_solve_with_its_last_iterate():
     with pytest.raises(L.CBSError):
         with CBSPlan(n, n, n, LAM / 8, LAM, 1.0, (8,) * 3, (8,) * 3) as plan:
             plan.set_time_limit(-1.0)
+
+
+def test_non_finite_source_ends_the_solve_as_diverged_and_the_plan_recovers():
+    """A user source holding a NaN (made on the host; no GPU fault) makes the residual
+    non-finite: the solve returns CBS_ERR_DIVERGED at the first check, and the next solve on
+    the same plan with a finite source runs normally."""
+    import torch
+    from paper_2506_15411_gb300 import CBSPlan, PlaneWave, UserSource
+    from paper_2506_15411_gb300 import _lib as L
+    nx, ny, nz = 24, 20, 16
+    eps = torch.from_numpy(inputs.random_eps(nx, ny, nz, seed=3)).cuda()
+    S = torch.zeros((3, nz, ny, nx), dtype=torch.complex64)
+    S[0, nz // 2, ny // 2, nx // 2] = complex(float("nan"), 0.0)
+    S = S.cuda()
+    with CBSPlan(nx, ny, nz, LAM / 8, LAM, 1.0, (3, 3, 3), (3, 3, 3), tol=1e-6, max_iter=64,
+                 check_every=8) as plan:
+        plan.set_permittivity(eps)
+        with pytest.raises(L.CBSError) as ei:
+            plan.forward(UserSource(S))
+        assert ei.value.code == L.CBS_ERR_DIVERGED and "diverged" in str(ei.value)
+        plan.set_solver(0.0, 16, 8)
+        E, s = plan.forward(PlaneWave())
+        torch.cuda.synchronize()
+    assert s.status == L.CBS_OK and s.iters == 16 and torch.isfinite(torch.view_as_real(E)).all()

@@ -132,3 +132,35 @@ def test_requests_are_admitted_while_others_run():
     later = first[3:]
     assert all(r.t_admit >= min(q.t_done for q in first[:3]) - 1e-3 for r in later)
     assert min(r.t_admit for r in later) < max(q.t_done for q in first[:3])
+
+
+def test_a_large_request_is_not_starved_by_a_stream_of_small_ones():
+    """With memory for the large request only while no small slot is held, later small
+    requests may pass it a bounded number of times (8); then admission waits for it."""
+    torch = _torch()
+    from paper_2506_15411_gb300 import PlaneWave
+    from paper_2506_15411_gb300.serve import GridSpec, Server
+    lam = 1.064e-6
+    small = GridSpec(32, 32, 32, lam / 8, lam, 1.0, (4, 4, 4), (4, 4, 4))
+    large = GridSpec(64, 64, 64, lam / 8, lam, 1.0, (8, 8, 8), (8, 8, 8))
+
+    def slot_bytes(g):   # the server's footprint of a slot: plan, eps, E, E_adj, gradient
+        nxp = (g.nx + 15) // 16 * 16
+        return nxp * g.ny * g.nz * 56 + g.nx * g.ny * g.nz * 56 + (16 << 20)
+
+    budget = (slot_bytes(large) + (1 << 20)) / 1e9
+    eps_s = inputs.random_eps(32, 32, 32, seed=21)
+    eps_l = inputs.random_eps(64, 64, 64, seed=22)
+    with Server(max_active=4, hbm_budget_gb=budget, tol=1e-3, check_every=16) as srv:
+        for i in range(2):
+            srv.submit(small, eps_s, PlaneWave(), (16, 16, 20), tag=("s", i))
+        srv.submit(large, eps_l, PlaneWave(), (32, 32, 40), tag=("L", 0))
+        for i in range(2, 26):
+            srv.submit(small, eps_s, PlaneWave(), (16, 16, 20), tag=("s", i))
+        res = {r.tag: r for r in srv.wait(26 + 1)}
+    torch.cuda.synchronize()
+    assert all(r.ok for r in res.values()), [r.error for r in res.values() if not r.ok]
+    big = res[("L", 0)]
+    passed = sum(1 for i in range(2, 26) if res[("s", i)].t_admit < big.t_admit)
+    assert passed <= 8, passed
+    assert big.fwd.iters > 0

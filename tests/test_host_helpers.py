@@ -37,12 +37,11 @@ def test_parse_size_and_percentiles():
 
 def test_traffic_is_reported_only_for_the_measured_sources(tmp_path, monkeypatch):
     rec = {"source_sha256": bench.source_digest(), "bytes_per_launch": {"k_zpass_green": 123}}
-    prof = tmp_path / "profiles"
-    prof.mkdir()
-    (prof / "traffic_fresnel_lens_275x275x315.json").write_text(json.dumps(rec))
-    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    path = tmp_path / "traffic.json"
+    path.write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "source_digest", lambda: rec["source_sha256"])
-    assert bench.load_traffic("k_zpass_green") == 123.0
-    assert bench.load_traffic("k_ypass_fwd") is None
+    assert bench.load_traffic("k_zpass_green", str(path)) == 123.0
+    assert bench.load_traffic("k_ypass_fwd", str(path)) is None
     monkeypatch.setattr(bench, "source_digest", lambda: "0" * 64)     # sources changed since
-    assert bench.load_traffic("k_zpass_green") is None
+    assert bench.load_traffic("k_zpass_green", str(path)) is None
+    assert bench.load_traffic("k_zpass_green", str(tmp_path / "missing.json")) is None

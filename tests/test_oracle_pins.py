@@ -242,3 +242,39 @@ def test_splitting_and_layer_profile():
     t = np.linspace(0, 1, 20001)
     integral = np.trapezoid(g.k_vac * smax * t ** 2 / 2.0, t) * L
     assert np.isclose(2 * integral, np.log(1e4), rtol=1e-6)
+
+
+def test_absorption_maps_each_axis_profile_and_adds_them_in_edges_and_corners():
+    """sigma(r) of a grid whose six faces all have different layer widths: a voxel inside one
+    layer only gets that axis' ramp at its depth, an edge voxel the sum of two, a corner
+    voxel the sum of three (an x/y/z mix-up, a low/high mix-up or a max rule fails here).
+    Expected values are layer_strength(L) (t/L)^2 written out per voxel: depth t counts 1 at
+    the innermost layer voxel and L on the outer face."""
+    g = co.Grid(20, 24, 28, LAM / 8, LAM, 1.0, (2, 3, 4), (5, 6, 7))
+    sig = co.absorption(g)      # (nz, ny, nx)
+    S = co.layer_strength
+
+    def at(x, y, z):
+        return sig[z, y, x]
+
+    # interior: nothing
+    assert at(10, 12, 14) == 0.0
+    # x only: low face width 2 (x = 0 is depth 2), high face width 5 (x = 19 is depth 5)
+    assert np.isclose(at(0, 12, 14), S(g, 2) * (2 / 2) ** 2)
+    assert np.isclose(at(1, 12, 14), S(g, 2) * (1 / 2) ** 2)
+    assert np.isclose(at(17, 12, 14), S(g, 5) * (3 / 5) ** 2)
+    # y only: low width 3, high width 6 (y = 23 is depth 6, y = 18 depth 1)
+    assert np.isclose(at(10, 1, 14), S(g, 3) * (2 / 3) ** 2)
+    assert np.isclose(at(10, 18, 14), S(g, 6) * (1 / 6) ** 2)
+    assert at(10, 17, 14) == 0.0 and at(10, 3, 14) == 0.0
+    # z only: low width 4, high width 7 (z = 21 is depth 1)
+    assert np.isclose(at(10, 12, 2), S(g, 4) * (2 / 4) ** 2)
+    assert np.isclose(at(10, 12, 21), S(g, 7) * (1 / 7) ** 2)
+    assert at(10, 12, 20) == 0.0 and at(10, 12, 4) == 0.0
+    # edge (x low, z high): the two ramps add
+    assert np.isclose(at(0, 12, 27), S(g, 2) + S(g, 7))
+    # corner (x high depth 2, y low depth 3, z low depth 1): all three add
+    want = S(g, 5) * (2 / 5) ** 2 + S(g, 3) * (3 / 3) ** 2 + S(g, 4) * (1 / 4) ** 2
+    assert np.isclose(at(16, 0, 3), want)
+    # the strengths differ per width, so the checks above separate the axes
+    assert len({round(S(g, L), 9) for L in (2, 3, 4, 5, 6, 7)}) == 6

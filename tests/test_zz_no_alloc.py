@@ -19,8 +19,8 @@ pytestmark = pytest.mark.gpu
 LAM = 1.064e-6
 
 
-def _desc(L, nx, ny, nz, pitch, lo, hi, stream=0):
-    return L.cbs_plan_desc(nx, ny, nz, pitch, LAM, 1.0, (ctypes.c_int * 3)(*lo), (ctypes.c_int * 3)(*hi),
+def _desc(L, nx, ny, nz, pitch, lo, hi, stream=0, n_bg=1.0):
+    return L.cbs_plan_desc(nx, ny, nz, pitch, LAM, n_bg, (ctypes.c_int * 3)(*lo), (ctypes.c_int * 3)(*hi),
                            0.0, 1, 1, ctypes.c_void_p(stream))
 
 
@@ -38,15 +38,17 @@ def test_noalloc_splitting_matches_plan_on_two_calls_in_a_row():
     from paper_2506_15411_gb300 import _lib as L
     lib = L.lib()
     # a large grid first (many block partials), then a small one that reuses fewer of them
-    cases = [((96, 80, 110), LAM / 8, (8, 6, 10), (7, 8, 9), 1.0, 2.4, 31),
-             ((20, 18, 22), LAM / 6, (3, 2, 4), (2, 3, 1), 1.3, 1.6, 32)]
-    for (nx, ny, nz), pitch, lo, hi, emin, emax, seed in cases:
+    # (a third grid with a background index other than 1 checks the layer strength's n_bg)
+    cases = [((96, 80, 110), LAM / 8, (8, 6, 10), (7, 8, 9), 1.0, 2.4, 31, 1.0),
+             ((20, 18, 22), LAM / 6, (3, 2, 4), (2, 3, 1), 1.3, 1.6, 32, 1.0),
+             ((40, 36, 30), LAM / 8, (4, 5, 6), (6, 5, 4), 1.7, 2.2, 34, 1.33)]
+    for (nx, ny, nz), pitch, lo, hi, emin, emax, seed, n_bg in cases:
         eps = torch.from_numpy(inputs.random_eps(nx, ny, nz, lo=emin, hi=emax, seed=seed)).cuda()
-        with CBSPlan(nx, ny, nz, pitch, LAM, 1.0, lo, hi) as plan:
+        with CBSPlan(nx, ny, nz, pitch, LAM, n_bg, lo, hi) as plan:
             plan.set_permittivity(eps)
             k0_ref, ep_ref = plan.splitting()
         torch.cuda.synchronize()
-        rc, k0, ep = _noalloc(L, lib, _desc(L, nx, ny, nz, pitch, lo, hi), eps)
+        rc, k0, ep = _noalloc(L, lib, _desc(L, nx, ny, nz, pitch, lo, hi, n_bg=n_bg), eps)
         assert rc == L.CBS_OK, lib.cbs_last_error()
         assert abs(k0 - k0_ref) <= 1e-12 * abs(k0_ref)
         assert abs(ep - ep_ref) <= 1e-12 * ep_ref
@@ -65,6 +67,13 @@ def test_noalloc_rejects_grids_beyond_its_scratch():
     bad[1, 2, 3] = float("inf")
     rc, _, _ = _noalloc(L, lib, _desc(L, 6, 6, 6, LAM / 8, (1, 1, 1), (1, 1, 1)), bad)
     assert rc == L.CBS_ERR_ARG and b"non-finite" in lib.cbs_last_error()
+    # pads that cbs_plan rejects (over half the axis) are rejected here too
+    from paper_2506_15411_gb300 import CBSPlan
+    for lo, hi in (((4, 1, 1), (1, 1, 1)), ((1, 1, 1), (1, 1, 4))):
+        with pytest.raises(L.CBSError):
+            CBSPlan(7, 7, 7, LAM / 8, LAM, 1.0, lo, hi)
+        rc, _, _ = _noalloc(L, lib, _desc(L, 7, 7, 7, LAM / 8, lo, hi), eps)
+        assert rc == L.CBS_ERR_ARG and b"pads" in lib.cbs_last_error()
     # the scratch is still good after the rejected calls
     eps = torch.from_numpy(inputs.random_eps(12, 10, 14, seed=33)).cuda()
     rc, k0, ep = _noalloc(L, lib, _desc(L, 12, 10, 14, LAM / 8, (2, 2, 2), (2, 2, 2)), eps)
