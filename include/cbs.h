@@ -60,11 +60,8 @@ typedef struct cbs_plan_s* cbs_plan_t;
 /* Problem and solver description (copied by cbs_plan). */
 typedef struct {
   int nx, ny, nz;         /* grid, including the absorbing layers; each a product of
-                             2, 3, 5, 7, 11, 13 and at most 1024.  nz is further bounded by
-                             the z tiles (whole z columns of 3 components, double-buffered,
-                             in shared memory): every such nz <= 714 is supported, longer
-                             ones (up to 756) only where the tensor-copy boxes divide nz;
-                             cbs_plan returns CBS_ERR_ARG for the others */
+                             2, 3, 5, 7, 11, 13 and at most 1024 (cbs_plan returns
+                             CBS_ERR_ARG for others) */
   double pitch_m;         /* voxel pitch [m] (isotropic) */
   double lambda_m;        /* vacuum wavelength [m] */
   double n_bg;            /* background index; sets the layer strength */
@@ -75,6 +72,19 @@ typedef struct {
   int max_iter;           /* > 0 */
   int check_every;        /* iterations between residual checks on the host (>= 1) */
   void* cuda_stream;      /* cudaStream_t the plan works on; NULL = legacy (see above) */
+  /* Absorbing layers (the paper gives their thickness, not their profile).  A voxel at depth
+   * t (1 .. L) into a layer of L voxels gets k^2 = k_vac^2 (eps_r + i sigma) with
+   * sigma = sigma_max (t/L)^p and sigma_max = (p+1) n_bg ln(1/layer_round_trip) / (k_vac L pitch):
+   * a normally incident plane wave keeps the amplitude layer_round_trip after crossing the
+   * layer and back (weak-absorption estimate).  That bounds the reflection of a layer several
+   * wavelengths thick (measured 1.2e-4 for 1e-4 at 6 lambda); a layer one wavelength thick
+   * reflects more through its gradient (about 5 % for 1e-4, 0.4 - 2 % for 1e-2).  The
+   * absorption raises the series' shift epsilon, and the iteration count with it: weaker or
+   * non-adding layers converge in fewer iterations.  Zero-initialised fields select the
+   * defaults. */
+  double layer_round_trip;  /* in (0, 1); 0 selects 1e-4 */
+  double layer_power;       /* ramp exponent p in (0, 16]; 0 selects 2 */
+  int layer_corner_max;     /* where layers overlap: 0 their profiles add, 1 the largest applies */
 } cbs_plan_desc;
 
 #define CBS_SRC_PLANE_WAVE 0  /* current sheet on plane z_plane launching pol * exp(ik|z-z_s|) */
@@ -300,6 +310,9 @@ typedef struct {
   int nx, ny, nz;           /* grid and physics as in cbs_plan_desc */
   double pitch_m, lambda_m, n_bg;
   int pad_lo[3], pad_hi[3];
+  double layer_round_trip;  /* absorbing layers as in cbs_plan_desc (0: defaults) */
+  double layer_power;
+  int layer_corner_max;
   const float* eps_host;    /* permittivity float32 [nz][ny][nx]: exactly one of eps_host */
   const float* eps_dev;     /* (read with a blocking copy at admission) and eps_dev */
   cbs_source src;           /* plane wave or point source; warm_start 0 */

@@ -76,6 +76,11 @@ class Grid:
     n_bg: float = 1.0     # background refractive index (sets the layer strength)
     pad_lo: tuple = (0, 0, 0)
     pad_hi: tuple = (0, 0, 0)
+    # absorbing-layer profile (READING, see layer_strength): the round-trip amplitude a
+    # normally incident plane wave keeps, the ramp exponent, and the rule where layers overlap
+    round_trip: float = 1e-4
+    power: float = 2.0
+    corner: str = "sum"   # "sum": the axis profiles add; "max": the largest applies
 
     @property
     def k_vac(self) -> float:
@@ -96,36 +101,46 @@ class Grid:
 def layer_strength(grid: Grid, thickness_vox: int) -> float:
     """Peak absorption sigma_max of one layer of the given thickness.
 
-    READING (the paper gives no profile): k^2 gains i k_vac^2 sigma_max (t/L)^2 at depth t
-    into a layer of thickness L.  For weak absorption Im k = k_vac sigma / (2 n_bg), so the
-    one-way attenuation exponent is k_vac sigma_max L / (6 n_bg); sigma_max is set so that
-    the round trip through the layer attenuates the amplitude by 1e4.
+    READING (the paper gives no profile): k^2 gains i k_vac^2 sigma_max (t/L)^p at depth t
+    into a layer of thickness L (p = grid.power, 2 by default).  For weak absorption
+    Im k = k_vac sigma / (2 n_bg), so the one-way attenuation exponent is
+    k_vac sigma_max L / (2 (p + 1) n_bg); sigma_max is set so that the round trip through the
+    layer leaves the amplitude grid.round_trip (1e-4 by default).
     """
     L = thickness_vox * grid.pitch
-    return 3.0 * grid.n_bg * LN_1E4 / (grid.k_vac * L)
+    log_rt = LN_1E4 if grid.round_trip == 1e-4 else math.log(1.0 / grid.round_trip)
+    return (grid.power + 1.0) * grid.n_bg * log_rt / (grid.k_vac * L)
+
+
+def _ramp(t: float, p: float) -> float:
+    return t * t if p == 2.0 else t ** p
 
 
 def axis_profile(grid: Grid, n: int, lo: int, hi: int) -> np.ndarray:
-    """sigma along one axis: zero in the interior, quadratic ramp in each layer.
+    """sigma along one axis: zero in the interior, a ramp (t / thickness)^p in each layer.
 
     Voxel i < lo sits at depth t = lo - i (1..lo) into the low layer; voxel i >= n - hi at
-    depth t = i - (n - hi - 1) (1..hi) into the high layer; the ramp is (t / thickness)^2.
+    depth t = i - (n - hi - 1) (1..hi) into the high layer.
     """
     s = np.zeros(n)
     for i in range(n):
         if i < lo:
-            s[i] = layer_strength(grid, lo) * ((lo - i) / lo) ** 2
+            s[i] = layer_strength(grid, lo) * _ramp((lo - i) / lo, grid.power)
         elif i >= n - hi:
-            s[i] = layer_strength(grid, hi) * ((i - (n - hi - 1)) / hi) ** 2
+            s[i] = layer_strength(grid, hi) * _ramp((i - (n - hi - 1)) / hi, grid.power)
     return s
 
 
 def absorption(grid: Grid) -> np.ndarray:
     """sigma(r) on the grid.  READING: where layers overlap (edges, corners) the per-axis
-    profiles add."""
+    profiles add (grid.corner = "sum", the default) or the largest applies ("max")."""
     sx = axis_profile(grid, grid.nx, grid.pad_lo[0], grid.pad_hi[0])
     sy = axis_profile(grid, grid.ny, grid.pad_lo[1], grid.pad_hi[1])
     sz = axis_profile(grid, grid.nz, grid.pad_lo[2], grid.pad_hi[2])
+    if grid.corner == "max":
+        return np.maximum(np.maximum(sz[:, None, None], sy[None, :, None]), sx[None, None, :])
+    if grid.corner != "sum":
+        raise ValueError(f"corner rule {grid.corner!r}")
     return sz[:, None, None] + sy[None, :, None] + sx[None, None, :]
 
 

@@ -48,7 +48,8 @@ class cbs_plan_desc(Structure):
                 ("pitch_m", c_double), ("lambda_m", c_double), ("n_bg", c_double),
                 ("pad_lo", c_int * 3), ("pad_hi", c_int * 3),
                 ("tol", c_double), ("max_iter", c_int), ("check_every", c_int),
-                ("cuda_stream", c_void_p)]
+                ("cuda_stream", c_void_p),
+                ("layer_round_trip", c_double), ("layer_power", c_double), ("layer_corner_max", c_int)]
 
 
 class cbs_source(Structure):
@@ -76,6 +77,7 @@ class cbs_request(Structure):
     _fields_ = [("nx", c_int), ("ny", c_int), ("nz", c_int),
                 ("pitch_m", c_double), ("lambda_m", c_double), ("n_bg", c_double),
                 ("pad_lo", c_int * 3), ("pad_hi", c_int * 3),
+                ("layer_round_trip", c_double), ("layer_power", c_double), ("layer_corner_max", c_int),
                 ("eps_host", c_void_p), ("eps_dev", c_void_p), ("src", cbs_source), ("adjoint", c_int),
                 ("r0", c_int * 3), ("E_host", c_void_p), ("E_dev", c_void_p), ("grad_host", c_void_p),
                 ("grad_dev", c_void_p)]

@@ -29,6 +29,8 @@
 #include <vector>
 
 #include "../../include/cbs.h"
+#include "absorber.h"
+#include "axis_plan.h"
 #include "plan.h"
 #include "tma.cuh"
 
@@ -50,77 +52,21 @@ constexpr double kPiD = 3.14159265358979323846;
 #ifndef CBS_MIN_OCC2_TX
 #define CBS_MIN_OCC2_TX 8
 #endif
+#ifndef CBS_YZ_MAX_BUF
+#define CBS_YZ_MAX_BUF 4
+#endif
+#ifndef CBS_X_SETS
+#define CBS_X_SETS 3
+#endif
+#ifndef CBS_X_MIN_ROWS
+#define CBS_X_MIN_ROWS 2
+#endif
 constexpr int kMaxYZOcc = CBS_MAX_YZ_OCC;    // a build with 1 keeps every y/z kernel at one block per SM
 constexpr int kMinOcc2Tx = CBS_MIN_OCC2_TX;  // narrowest tile worth two blocks per SM
+constexpr int kYZMaxBuf = CBS_YZ_MAX_BUF;    // most tile buffers of a y or z block
+constexpr int kXSets = CBS_X_SETS;           // most buffer sets of an x block ...
+constexpr int kXMinRows = CBS_X_MIN_ROWS;    // ... while its tiles keep at least this many rows
 constexpr int kMaxN = 1024;
-
-// Factor n into the supported radices (at most max_radix): fewest stages first, then the
-// largest smallest radix (fewest threads per transform).  Radices are stored largest first.
-bool factor_axis(int n, int max_radix, AxisPlan& out) {
-  static const int cand[] = {16, 13, 12, 11, 10, 9, 8, 7, 6, 5, 4, 3, 2};
-  out = AxisPlan{};
-  out.n = n;
-  if (n == 1) {
-    out.ns = 1;
-    out.r[0] = 1;
-    out.T = 1;
-    return true;
-  }
-  std::vector<int> cur, best;
-  std::function<void(int, int)> dfs;
-  auto better = [&](const std::vector<int>& a, const std::vector<int>& b) {
-    if (b.empty()) return true;
-    if (a.size() != b.size()) return a.size() < b.size();
-    const int ma = *std::min_element(a.begin(), a.end());
-    const int mb = *std::min_element(b.begin(), b.end());
-    return ma > mb;
-  };
-  dfs = [&](int rem, int maxr) {
-    if (rem == 1) {
-      if (better(cur, best)) best = cur;
-      return;
-    }
-    if ((int)cur.size() >= kMaxStages) return;
-    for (int r : cand) {
-      if (r > maxr || r > max_radix || rem % r) continue;
-      cur.push_back(r);
-      dfs(rem / r, r);
-      cur.pop_back();
-    }
-  };
-  dfs(n, 1 << 30);
-  if (best.empty()) return false;
-  out.ns = (int)best.size();
-  int rmin = 1 << 30;
-  for (int i = 0; i < out.ns; ++i) {
-    out.r[i] = best[i];
-    rmin = std::min(rmin, best[i]);
-  }
-  out.T = n / rmin;
-  return true;
-}
-
-int float_bits(float f) {
-  int i;
-  std::memcpy(&i, &f, sizeof(i));
-  return i;
-}
-
-// Device table of an axis plan: per stage {r, Ns, n / r, n / (Ns r)} and
-// {bits of 1 / (n / r), bits of 1 / Ns, 0, 0}.
-std::vector<int4> stage_table(const AxisPlan& ap) {
-  std::vector<int4> t(2 * kMaxStages, make_int4(1, 1, 1, 1));
-  int Ns = 1;
-  for (int q = 0; q < ap.ns; ++q) {
-    const int r = ap.r[q];
-    const int stride = ap.n / r;
-    t[2 * q] = make_int4(r, Ns, stride, ap.n / (Ns * r));
-    t[2 * q + 1] = make_int4(float_bits(1.0f / (float)stride), float_bits(1.0f / (float)Ns), 0, 0);
-    Ns *= r;
-  }
-  return t;
-}
-
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
@@ -561,18 +507,21 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
   if (!(d.pitch_m > 0) || !(d.lambda_m > 0) || !(d.n_bg > 0))
     return fail(CBS_ERR_ARG, "pitch, wavelength and n_bg must be positive");
   if (d.max_iter < 1 || d.check_every < 1) return fail(CBS_ERR_ARG, "max_iter and check_every must be >= 1");
-  AxisPlan ax, ay, az;
-  if (!factor_axis(d.nx, 16, ax)) return fail(CBS_ERR_ARG, "nx = %d is not a product of 2,3,5,7,11,13", d.nx);
-  if (!factor_axis(d.ny, 16, ay)) return fail(CBS_ERR_ARG, "ny = %d is not a product of 2,3,5,7,11,13", d.ny);
-  if (!factor_axis(d.nz, 16, az)) return fail(CBS_ERR_ARG, "nz = %d is not a product of 2,3,5,7,11,13", d.nz);
-  if (ax.T > 512 || ay.T > 512 || az.T > 512)
-    return fail(CBS_ERR_ARG, "an axis needs more than 512 threads per transform (unsupported factorisation)");
+  const LayerSpec layers = layer_spec(d.layer_round_trip, d.layer_power, d.layer_corner_max);
+  if (!layer_spec_valid(layers))
+    return fail(CBS_ERR_ARG, "layer round trip %g, power %g or corner rule %d out of range", d.layer_round_trip,
+                d.layer_power, d.layer_corner_max);
+  std::vector<int> rad[3];
+  for (int a2 = 0; a2 < 3; ++a2)
+    if (!factor_radices(dims[a2], 16, rad[a2]))
+      return fail(CBS_ERR_ARG, "axis %d size %d is not a product of 2,3,5,7,11,13", a2, dims[a2]);
 
   cbs_plan_s* p = new cbs_plan_s();
   p->d = d;
   p->N = (size_t)d.nx * d.ny * d.nz;
   p->pitch = d.pitch_m;
   p->kvac = 2.0 * kPiD / d.lambda_m;
+  p->layers = layers;
   p->user_stream = static_cast<cudaStream_t>(d.cuda_stream);
   auto bail = [&](int code) {
     cbs_destroy(p);
@@ -604,19 +553,28 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
   a.ny = d.ny;
   a.nz = d.nz;
   a.N = p->N;
-  a.ax = ax;
-  a.ay = ay;
-  a.az = az;
-  // launch shapes: persistent, double-buffered tile kernels, one block per SM (about 220 KB
-  // of shared memory each): x tiles of rpb rows, y and z tiles of TX columns by whole
-  // tensor-copy boxes, TX as wide as fits
+  // launch shapes: persistent tile kernels with rings of tile buffers (the FFTs run in place,
+  // so a tile needs no scratch): x tiles of rpb rows, y and z tiles of TX columns by whole
+  // tensor-copy boxes
   const size_t kBlockBudget = 220 * 1024, kBlockBudget2 = 110 * 1024;
   a.nxp = round_up(d.nx, 16);
   a.Nw = (size_t)a.nxp * d.ny * d.nz;
+  const int twb[3] = {round_up(d.nx * (int)sizeof(float2), 16), round_up(d.ny * (int)sizeof(float2), 16),
+                      round_up(d.nz * (int)sizeof(float2), 16)};
   {
-    const size_t per_row = (size_t)17 * a.nxp * sizeof(float2);   // the inverse x tile: 2 x 7 + 3 arrays
-    const size_t fixed = (size_t)round_up(d.nx * (int)sizeof(float2), 16) + 24 + 32 * 8;
-    a.rpb = (int)std::max<size_t>(1, std::min<size_t>(64, (kBlockBudget - fixed) / per_row));
+    // x: nset buffer sets of 7 arrays [rpb][nxp] (W and E of 3 components, V); the most sets
+    // (up to kXSets) that still hold tiles of at least kXMinRows rows, then the most rows
+    const size_t fixed = (size_t)twb[0] + 8 * 4 + 8 + 32 * 8;
+    const size_t row7 = (size_t)7 * a.nxp * sizeof(float2);
+    a.nset_x = 2;
+    for (int ns = kXSets; ns >= 2; --ns)
+      if ((kBlockBudget - fixed) / (ns * row7) >= (size_t)kXMinRows || ns == 2) {
+        a.nset_x = ns;
+        break;
+      }
+    a.rpb = (int)std::max<size_t>(1, std::min<size_t>(64, (kBlockBudget - fixed) / (a.nset_x * row7)));
+    const size_t row4 = (size_t)4 * a.rpb * a.nxp * sizeof(float2);
+    a.nset_xf = (int)std::max<size_t>(2, std::min<size_t>(4, (kBlockBudget - fixed) / row4));
   }
   // y and z tiles: TX columns x whole axis, brought in by boxes of B rows.  B is a divisor of
   // the axis in [16, 64] when one keeps every box's shared-memory offset (B TX 8 bytes) a
@@ -628,32 +586,28 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
       if (n % b == 0 && (b * tx) % 16 == 0) return b;
     return kBoxRows;
   };
-  const size_t twy_b = round_up(d.ny * (int)sizeof(float2), 16), twz_b = round_up(d.nz * (int)sizeof(float2), 16);
+  const int pqbz = round_up(d.nz * (int)sizeof(float2), 16);
   auto ysmem = [&](int tx, int nb) {
     const int rows = round_up(d.ny, box_rows(d.ny, tx));
-    return (size_t)(nb * rows + d.ny) * tx * sizeof(float2) + twy_b + 8 * nb + 8;
+    return (size_t)nb * rows * tx * sizeof(float2) + twb[1] + 8 * nb + 8;
   };
   auto zsmem = [&](int tx, int nb) {
-    return (size_t)3 * (nb + 1) * round_up(d.nz, box_rows(d.nz, tx)) * tx * sizeof(float2) + twz_b + 8 * nb + 8;
+    return (size_t)3 * nb * round_up(d.nz, box_rows(d.nz, tx)) * tx * sizeof(float2) + twb[2] + pqbz + 8 * nb + 8;
   };
-  auto max_radix = [](const AxisPlan& ap) {
-    int m = 1;
-    for (int i = 0; i < ap.ns; ++i) m = std::max(m, ap.r[i]);
-    return m;
-  };
+  auto max_radix = [](const std::vector<int>& r) { return *std::max_element(r.begin(), r.end()); };
   // Two blocks per SM (half the shared memory each) when the axis needs no radix above 11,
-  // else one: the widest tile, then the most buffers, that fits.
+  // else one: the widest tile, then the most buffers (2 .. kYZMaxBuf), that fits.
   auto pick = [&](auto smem, int maxr, int& tx, int& nb, int& occ) {
     for (occ = (maxr <= 11 && kMaxYZOcc >= 2) ? 2 : 1; occ >= 1; --occ) {
       const size_t budget = occ == 2 ? kBlockBudget2 : kBlockBudget;
       for (tx = 16; tx >= (occ == 2 ? kMinOcc2Tx : 4); tx /= 2)
-        for (nb = 3; nb >= 2; --nb)
+        for (nb = kYZMaxBuf; nb >= 2; --nb)
           if (smem(tx, nb) <= budget) return true;
     }
     return false;
   };
-  const bool fy = pick(ysmem, max_radix(ay), a.tx_y, a.nbuf_y, a.occ_y);
-  const bool fz = pick(zsmem, max_radix(az), a.tx_z, a.nbuf_z, a.occ_z);
+  const bool fy = pick(ysmem, max_radix(rad[1]), a.tx_y, a.nbuf_y, a.occ_y);
+  const bool fz = pick(zsmem, 16, a.tx_z, a.nbuf_z, a.occ_z);   // the z pass runs at one block per SM
   if (!fy || !fz) {
     fail(CBS_ERR_ARG, "axis too long for the shared-memory tiles");
     return bail(CBS_ERR_ARG);
@@ -662,6 +616,10 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
   a.zb = box_rows(d.nz, a.tx_z);
   a.nyr = round_up(d.ny, a.yb);
   a.nzr = round_up(d.nz, a.zb);
+  a.twbx = twb[0];
+  a.twby = twb[1];
+  a.twbz = twb[2];
+  a.pqbz = pqbz;
 
   const size_t N = p->N;
   CKP(cudaMalloc(&p->V, a.Nw * sizeof(float2)));
@@ -693,42 +651,48 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
   CKP(cudaMalloc(&p->pbad, p->red_blocks * sizeof(int)));
   CKP(cudaMalloc(&p->pdev, p->red_blocks * sizeof(double)));
 
-  // twiddles exp(-2 pi i m / n) in FP64, rounded to FP32; each axis' table starts on a
-  // 128-byte boundary and is copied whole into the tiles' shared memory (n * 8 bytes rounded
-  // up to a multiple of 16)
-  int twoff[3], twlen[3], twtot = 0;
-  for (int a2 = 0; a2 < 3; ++a2) {
-    twoff[a2] = twtot;
-    twlen[a2] = round_up(dims[a2] * (int)sizeof(float2), 16);
-    twtot += round_up(twlen[a2], 128);
-  }
-  std::vector<float2> tw(twtot / sizeof(float2), make_float2(0.f, 0.f));
-  for (int a2 = 0; a2 < 3; ++a2) {
-    const int n = dims[a2];
-    for (int m = 0; m < n; ++m) {
-      const double ang = -2.0 * kPiD * (double)m / (double)n;
-      tw[twoff[a2] / sizeof(float2) + m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-    }
-  }
-  CKP(cudaMalloc(&p->tw, twtot));
-  CKP(cudaMemcpy(p->tw, tw.data(), twtot, cudaMemcpyHostToDevice));
-  a.twx = p->tw + twoff[0] / sizeof(float2);
-  a.twy = p->tw + twoff[1] / sizeof(float2);
-  a.twz = p->tw + twoff[2] / sizeof(float2);
-  a.twbx = twlen[0];
-  a.twby = twlen[1];
-  a.twbz = twlen[2];
-  CKP(cudaMalloc(&p->stages, 3 * 2 * kMaxStages * sizeof(int4)));
+  // per-axis FFT tables (axis_plan.h): radix order for the axis' shared-memory layout, stage
+  // table, per-stage twiddles (FP64, rounded; padded to n entries so that a fixed n * 8 bytes
+  // are copied into the tiles) and the wave numbers of each spectrum position (padded to 16
+  // entries); every table starts on a 128-byte boundary
   {
-    std::vector<int4> all;
-    for (const AxisPlan* ap : {&a.ax, &a.ay, &a.az}) {
-      std::vector<int4> t = stage_table(*ap);
-      all.insert(all.end(), t.begin(), t.end());
+    const AxisLayout lay[3] = {AxisLayout::Rows, AxisLayout::Cols, AxisLayout::ColsZ};
+    const int ncol[3] = {0, a.tx_y, a.tx_z};
+    std::vector<int4> st_all(3 * 2 * kMaxAxisStages, make_int4(1, 1, 1, 0));
+    std::vector<float2> tw_all, pq_all;
+    int twoff[3], pqoff[3];
+    for (int a2 = 0; a2 < 3; ++a2) {
+      const int n = dims[a2];
+      p->radix_order[a2] = order_radices(rad[a2], n, lay[a2], ncol[a2]);
+      std::vector<int4> st;
+      std::vector<float2> tw, pq;
+      axis_tables(n, p->radix_order[a2], st, tw, pq);
+      std::copy(st.begin(), st.end(), st_all.begin() + a2 * 2 * kMaxAxisStages);
+      twoff[a2] = (int)tw_all.size();
+      tw.resize(round_up(n, 16), make_float2(0.f, 0.f));
+      tw_all.insert(tw_all.end(), tw.begin(), tw.end());
+      pqoff[a2] = (int)pq_all.size();
+      pq.resize(round_up(n, 16), make_float2(0.f, 0.f));
+      pq_all.insert(pq_all.end(), pq.begin(), pq.end());
+      AxisIP& ap = a2 == 0 ? a.ax : (a2 == 1 ? a.ay : a.az);
+      ap.n = n;
+      ap.ns = (int)p->radix_order[a2].size();
     }
-    CKP(cudaMemcpy(p->stages, all.data(), all.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    CKP(cudaMalloc(&p->tw, tw_all.size() * sizeof(float2)));
+    CKP(cudaMemcpy(p->tw, tw_all.data(), tw_all.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    CKP(cudaMalloc(&p->pq, pq_all.size() * sizeof(float2)));
+    CKP(cudaMemcpy(p->pq, pq_all.data(), pq_all.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    CKP(cudaMalloc(&p->stages, st_all.size() * sizeof(int4)));
+    CKP(cudaMemcpy(p->stages, st_all.data(), st_all.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    a.twx = p->tw + twoff[0];
+    a.twy = p->tw + twoff[1];
+    a.twz = p->tw + twoff[2];
+    a.pqx = p->pq + pqoff[0];
+    a.pqy = p->pq + pqoff[1];
+    a.pqz = p->pq + pqoff[2];
     a.ax.st = p->stages;
-    a.ay.st = p->stages + 2 * kMaxStages;
-    a.az.st = p->stages + 4 * kMaxStages;
+    a.ay.st = p->stages + 2 * kMaxAxisStages;
+    a.az.st = p->stages + 4 * kMaxAxisStages;
   }
 
   // persistent grid sizes (occupancy of each tile kernel at its shared-memory size)
@@ -744,7 +708,7 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
   // a multiple of 16 (checked here once: these pointers and sizes are fixed for the plan)
   {
     auto a16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
-    const bool ok = a16(a.twx) && a16(a.twy) && a16(a.twz) && a16(p->Ei) && a16(p->V) && a16(p->W) &&
+    const bool ok = a16(a.twx) && a16(a.twy) && a16(a.twz) && a16(a.pqz) && a16(p->Ei) && a16(p->V) && a16(p->W) &&
                     (a.twbx % 16 == 0) && (a.twby % 16 == 0) && (a.twbz % 16 == 0) &&
                     ((size_t)a.nxp * sizeof(float2)) % 16 == 0 && (a.Nw * sizeof(float2)) % 16 == 0;
     if (!ok) {
@@ -753,22 +717,13 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
     }
   }
 
-  // absorbing layers: sigma = sigma_max (t / L)^2 at depth t voxels into a layer of L voxels,
-  // sigma_max = 3 n_bg ln(1e4) / (k_vac L pitch) (round-trip amplitude 1e-4), summed over axes
+  // absorbing layers (absorber.h): sigma along each axis; the set-up kernels combine the three
   for (int a2 = 0; a2 < 3; ++a2) {
     const int n = dims[a2], lo = d.pad_lo[a2], hi = d.pad_hi[a2];
+    const double slo = layer_sigma_max(p->layers, d.n_bg, p->kvac, lo, d.pitch_m);
+    const double shi = layer_sigma_max(p->layers, d.n_bg, p->kvac, hi, d.pitch_m);
     std::vector<double> s(n, 0.0);
-    for (int i = 0; i < n; ++i) {
-      if (i < lo) {
-        const double smax = 3.0 * d.n_bg * std::log(1.0e4) / (p->kvac * lo * d.pitch_m);
-        const double t = (double)(lo - i) / lo;
-        s[i] = smax * t * t;
-      } else if (i >= n - hi) {
-        const double smax = 3.0 * d.n_bg * std::log(1.0e4) / (p->kvac * hi * d.pitch_m);
-        const double t = (double)(i - (n - hi - 1)) / hi;
-        s[i] = smax * t * t;
-      }
-    }
+    for (int i = 0; i < n; ++i) s[i] = layer_axis_sigma(i, n, lo, hi, slo, shi, p->layers.power);
     double* dst = a2 == 0 ? p->sx : (a2 == 1 ? p->sy : p->sz);
     CKP(cudaMemcpy(dst, s.data(), n * sizeof(double), cudaMemcpyHostToDevice));
   }
@@ -790,7 +745,7 @@ void cbs_destroy(cbs_plan_t p) {
   cudaSetDevice(p->device);
   if (p->stream) cudaStreamSynchronize(p->stream);
   drop_graphs(p);
-  void* devs[] = {p->V, p->W, p->Ei, p->tw, p->stages, p->partials, p->counter, p->hist, p->adj_amp, p->dobj,
+  void* devs[] = {p->V, p->W, p->Ei, p->tw, p->pq, p->stages, p->partials, p->counter, p->hist, p->adj_amp, p->dobj,
                   p->sx, p->sy, p->sz, p->pmin, p->pmax, p->pbad, p->pdev, p->eps_dev,
                   p->Ef, p->Ea, p->grad_dev, p->err_dev};
   for (void* q : devs)
@@ -891,7 +846,8 @@ int cbs_set_permittivity(cbs_plan_t p, const float* eps) {
   }
   const double kv2 = (p->kvac * p->pitch) * (p->kvac * p->pitch);
   const double k0sq = 0.5 * kv2 * (lo + hi);
-  CK(launch_k2_maxdev(eps, p->d.nx, p->d.ny, p->d.nz, p->sx, p->sy, p->sz, kv2, k0sq, p->pdev, B, p->stream));
+  CK(launch_k2_maxdev(eps, p->d.nx, p->d.ny, p->d.nz, p->sx, p->sy, p->sz, p->layers.corner_max, kv2, k0sq,
+                      p->pdev, B, p->stream));
   std::vector<double> dv(B);
   CK(cudaMemcpyAsync(dv.data(), p->pdev, B * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
   CK(cudaStreamSynchronize(p->stream));
@@ -899,8 +855,8 @@ int cbs_set_permittivity(cbs_plan_t p, const float* eps) {
   for (int b = 0; b < B; ++b) epsilon = std::max(epsilon, dv[b]);
   if (!(epsilon > 0.0) || !std::isfinite(epsilon))
     return fail(CBS_ERR_ARG, "epsilon = %g: a lossless homogeneous grid has no convergent splitting", epsilon);
-  CK(launch_build_v(eps, p->d.nx, p->d.ny, p->d.nz, p->base.nxp, p->sx, p->sy, p->sz, kv2, k0sq, epsilon, p->V,
-                    p->stream));
+  CK(launch_build_v(eps, p->d.nx, p->d.ny, p->d.nz, p->base.nxp, p->sx, p->sy, p->sz, p->layers.corner_max, kv2,
+                    k0sq, epsilon, p->V, p->stream));
   CK(cudaStreamSynchronize(p->stream));
   p->k0sq_s = k0sq;
   p->eps_s = epsilon;

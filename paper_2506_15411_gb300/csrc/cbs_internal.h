@@ -4,26 +4,11 @@
 #include <cuda_runtime.h>
 #include <cstddef>
 
+#include "fft_ip.cuh"
+
 namespace cbs {
 
-constexpr int kMaxStages = 8;
 constexpr int kBoxRows = 64;   // at most this many rows (y or z) per tensor-copy box
-
-// Stockham radix plan of one axis: n = r[0] * r[1] * ... * r[ns-1]; a transform is run
-// by T = n / min(r) threads, each doing at most one radix-r butterfly per stage.  Per stage
-// q: Ns[q] = r[0] * ... * r[q-1], stride[q] = n / r[q] (butterflies, and the distance
-// between a butterfly's inputs), twstep[q] = n / (Ns[q] r[q]).
-// The per-stage table lives in device memory, two int4 per stage: {r, Ns, stride, twstep}
-// and {bits of 1/stride, bits of 1/Ns, 0, 0} (float reciprocals for exact small-integer
-// division); it is read with uniform loads (a dynamically indexed kernel-parameter array
-// would be copied to the stack).
-struct AxisPlan {
-  int n;
-  int ns;
-  int T;
-  const int4* st;         // device table, 2 * ns entries
-  int r[kMaxStages];      // host copy of the radices
-};
 
 // Source term in the scaled units of the kernels (all k^2 quantities times pitch^2).
 struct SourceArgs {
@@ -44,11 +29,15 @@ struct IterArgs {
   size_t Nw;              // nxp * ny * nz: component stride of W
   int yb, zb;             // rows per tensor-copy box along y and z
   int nyr, nzr;           // ny, nz rounded up to whole boxes (shared-memory rows of a tile)
-  AxisPlan ax, ay, az;
-  const float2* twx;      // exp(-2 pi i m / n), m < n, per axis; each table 128-byte aligned
+  AxisIP ax, ay, az;      // in-place FFT plans (fft_ip.cuh)
+  const float2* twx;      // per-stage twiddle tables; each 128-byte aligned, padded to n entries
   const float2* twy;
   const float2* twz;
   int twbx, twby, twbz;   // bytes copied per table: n * 8 rounded up to a multiple of 16
+  const float2* pqx;      // wave numbers (p, q) of each position of an axis' spectrum,
+  const float2* pqy;      // padded with zeros to a multiple of 16 entries
+  const float2* pqz;
+  int pqbz;               // bytes of the z table the z pass copies (multiple of 16)
   float2* E;              // field being iterated, [3][nz][ny][nxp] (plan-owned copy)
   float2* W;              // workspace [3][nz][ny][nxp]
   const float2* V;        // potential [nz][ny][nxp], scaled
@@ -63,8 +52,9 @@ struct IterArgs {
   int* err;               // device error flag (a tensor-copy wait that timed out)
   // launch shapes
   int rpb;                // rows per tile, x passes
+  int nset_x, nset_xf;    // buffer sets of the x passes (inverse + forward; first forward)
   int tx_y, tx_z;         // x-columns per tile, y and z passes
-  int nbuf_y, nbuf_z;     // tile buffers of the pipelined y and z passes (2 or 3)
+  int nbuf_y, nbuf_z;     // tile buffers of the pipelined y and z passes (2 to 4)
   int occ_y, occ_z;       // blocks per SM of the y and z kernels (2: radices <= 11, 64 registers)
   int grid_x, grid_xf, grid_y, grid_z;   // persistent grid sizes (x inverse, x forward, y, z)
 };
@@ -87,10 +77,10 @@ cudaError_t x_grid_size(IterArgs& a, int sms);     // sets grid_x, grid_xf
 cudaError_t launch_eps_minmax(const float* eps, size_t N, float* part_min, float* part_max,
                               int* part_bad, int blocks, cudaStream_t s);
 cudaError_t launch_k2_maxdev(const float* eps, int nx, int ny, int nz, const double* sx,
-                             const double* sy, const double* sz, double kv2, double k0sq,
+                             const double* sy, const double* sz, int corner_max, double kv2, double k0sq,
                              double* part, int blocks, cudaStream_t s);
 cudaError_t launch_build_v(const float* eps, int nx, int ny, int nz, int nxp, const double* sx,
-                           const double* sy, const double* sz, double kv2, double k0sq,
+                           const double* sy, const double* sz, int corner_max, double kv2, double k0sq,
                            double eps_shift, float2* V, cudaStream_t s);
 cudaError_t launch_adjoint_amp(const float2* E, size_t N, int nx, int ny, int x, int y, int z,
                                float scale, float2* amp, cudaStream_t s);

@@ -1,7 +1,7 @@
 // fft_radix.cuh -- small in-register DFTs ("codelets") for the mixed-radix FFT passes.
 //
 // The 3D FFTs of the CBS iteration (the "N log N" cost of Fig. 1(b) of arXiv 2506.15411)
-// are built from Stockham stages whose butterflies are the DFTs below, applied to R values
+// are built from in-place DIF / DIT stages (fft_ip.cuh) whose butterflies are the DFTs below, applied to R values
 // held in registers.  Supported radices: 1 (identity), 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12,
 // 13, 16.
 //   - odd primes: symmetric-pair form, X[k] and X[R-k] share the sums over the pairs
@@ -13,25 +13,34 @@
 #include <cuda_runtime.h>
 #include <utility>
 
+// The codelets also compile for the host (the tests run the FFT stages on the CPU).
+#ifndef CBS_HD
+#if defined(__CUDACC__)
+#define CBS_HD __host__ __device__ __forceinline__
+#else
+#define CBS_HD inline
+#endif
+#endif
+
 namespace cbs {
 
 // ---------------------------------------------------------------- complex helpers
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+CBS_HD float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+CBS_HD float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+CBS_HD float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
-__device__ __forceinline__ float2 mul_i(float2 a) { return make_float2(-a.y, a.x); }      //  i a
-__device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }     // -i a
+CBS_HD float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+CBS_HD float2 mul_i(float2 a) { return make_float2(-a.y, a.x); }      //  i a
+CBS_HD float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }     // -i a
 
 // ---------------------------------------------------------------- compile-time loops
 template <class F, int... I>
-__device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, I...>) {
+CBS_HD void static_for_impl(F&& f, std::integer_sequence<int, I...>) {
   (f(std::integral_constant<int, I>{}), ...);
 }
 template <int N, class F>
-__device__ __forceinline__ void static_for(F&& f) {
+CBS_HD void static_for(F&& f) {
   static_for_impl(f, std::make_integer_sequence<int, N>{});
 }
 
@@ -63,7 +72,7 @@ constexpr double ct_cos(double x) {
 
 // a * w_R^M with w_R = exp(-2 pi i / R) (forward) or exp(+2 pi i / R) (inverse).
 template <int M, int R, bool INV>
-__device__ __forceinline__ float2 twc(float2 a) {
+CBS_HD float2 twc(float2 a) {
   constexpr int m = ((M % R) + R) % R;
   if constexpr (m == 0) {
     return a;
@@ -86,12 +95,12 @@ struct DFT;
 
 template <bool INV>
 struct DFT<1, INV> {
-  static __device__ __forceinline__ void run(float2*) {}
+  static CBS_HD void run(float2*) {}
 };
 
 template <bool INV>
 struct DFT<2, INV> {
-  static __device__ __forceinline__ void run(float2* v) {
+  static CBS_HD void run(float2* v) {
     float2 a = v[0], b = v[1];
     v[0] = cadd(a, b);
     v[1] = csub(a, b);
@@ -102,7 +111,7 @@ struct DFT<2, INV> {
 // A_k = x0 + sum_m cos(2 pi k m / R)(x_m + x_{R-m}), B_k = sum_m sin(2 pi k m / R)(x_m - x_{R-m}).
 template <int R, bool INV>
 struct DFTOdd {
-  static __device__ __forceinline__ void run(float2* v) {
+  static CBS_HD void run(float2* v) {
     constexpr int H = (R - 1) / 2;
     float2 a[H], b[H];
     float2 x0 = v[0];
@@ -150,7 +159,7 @@ template <bool INV> struct DFT<13, INV> : DFTOdd<13, INV> {};
 template <int R1, int R2, bool INV>
 struct DFTSplit {
   static constexpr int R = R1 * R2;
-  static __device__ __forceinline__ void run(float2* v) {
+  static CBS_HD void run(float2* v) {
     float2 y[R];
     static_for<R2>([&](auto n2i) {
       constexpr int n2 = decltype(n2i)::value;
@@ -193,7 +202,7 @@ template <bool INV> struct DFT<16, INV> : DFTSplit<4, 4, INV> {};
 // Radices above MAXR are not compiled in (a plan whose axes need them uses a MAXR = 16
 // kernel); leaving them out keeps the register allocation to what the smaller radices need.
 template <int MAXR = 16, class F>
-__device__ __forceinline__ void radix_dispatch(int r, F&& f) {
+CBS_HD void radix_dispatch(int r, F&& f) {
   switch (r) {
     case 1: f(std::integral_constant<int, 1>{}); break;
     case 2: f(std::integral_constant<int, 2>{}); break;

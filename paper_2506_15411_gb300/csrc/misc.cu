@@ -8,6 +8,7 @@
 // All k^2 quantities are in units of 1/pitch^2 (kv2 = (k_vac pitch)^2).
 #include <cfloat>
 #include <cstdint>
+#include "absorber.h"
 #include "cbs_internal.h"
 #include "tma.cuh"
 
@@ -59,7 +60,8 @@ __device__ __forceinline__ void voxel_xyz(size_t i, int nx, int ny, int& x, int&
 
 __global__ void k_k2_maxdev(const float* __restrict__ eps, int nx, int ny, int nz,
                             const double* __restrict__ sx, const double* __restrict__ sy,
-                            const double* __restrict__ sz, double kv2, double k0sq, double* part) {
+                            const double* __restrict__ sz, int corner_max, double kv2, double k0sq,
+                            double* part) {
   __shared__ double sh[32];
   const size_t N = (size_t)nx * ny * nz;
   double m = 0.0;
@@ -67,7 +69,7 @@ __global__ void k_k2_maxdev(const float* __restrict__ eps, int nx, int ny, int n
     int x, y, z;
     voxel_xyz(i, nx, ny, x, y, z);
     const double re = kv2 * (double)eps[i] - k0sq;
-    const double im = kv2 * (sx[x] + sy[y] + sz[z]);
+    const double im = kv2 * layer_combine(sx[x], sy[y], sz[z], corner_max);
     m = fmax(m, sqrt(re * re + im * im));
   }
   m = block_reduce(m, [](double p, double q) { return fmax(p, q); }, sh);
@@ -77,14 +79,14 @@ __global__ void k_k2_maxdev(const float* __restrict__ eps, int nx, int ny, int n
 // V in the padded row layout [nz][ny][nxp] of the iteration (the padding stays zero).
 __global__ void k_build_v(const float* __restrict__ eps, int nx, int ny, int nz, int nxp,
                           const double* __restrict__ sx, const double* __restrict__ sy,
-                          const double* __restrict__ sz, double kv2, double k0sq, double eshift,
-                          float2* __restrict__ V) {
+                          const double* __restrict__ sz, int corner_max, double kv2, double k0sq,
+                          double eshift, float2* __restrict__ V) {
   const size_t N = (size_t)nx * ny * nz;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
     int x, y, z;
     voxel_xyz(i, nx, ny, x, y, z);
     const double re = kv2 * (double)eps[i] - k0sq;
-    const double im = kv2 * (sx[x] + sy[y] + sz[z]) - eshift;
+    const double im = kv2 * layer_combine(sx[x], sy[y], sz[z], corner_max) - eshift;
     V[((size_t)z * ny + y) * nxp + x] = make_float2((float)re, (float)im);
   }
 }
@@ -151,16 +153,16 @@ cudaError_t launch_eps_minmax(const float* eps, size_t N, float* pmin, float* pm
 }
 
 cudaError_t launch_k2_maxdev(const float* eps, int nx, int ny, int nz, const double* sx,
-                             const double* sy, const double* sz, double kv2, double k0sq,
+                             const double* sy, const double* sz, int corner_max, double kv2, double k0sq,
                              double* part, int blocks, cudaStream_t s) {
-  k_k2_maxdev<<<blocks, 256, 0, s>>>(eps, nx, ny, nz, sx, sy, sz, kv2, k0sq, part);
+  k_k2_maxdev<<<blocks, 256, 0, s>>>(eps, nx, ny, nz, sx, sy, sz, corner_max, kv2, k0sq, part);
   return cudaGetLastError();
 }
 
 cudaError_t launch_build_v(const float* eps, int nx, int ny, int nz, int nxp, const double* sx,
-                           const double* sy, const double* sz, double kv2, double k0sq,
+                           const double* sy, const double* sz, int corner_max, double kv2, double k0sq,
                            double eshift, float2* V, cudaStream_t s) {
-  k_build_v<<<152 * 8, 256, 0, s>>>(eps, nx, ny, nz, nxp, sx, sy, sz, kv2, k0sq, eshift, V);
+  k_build_v<<<152 * 8, 256, 0, s>>>(eps, nx, ny, nz, nxp, sx, sy, sz, corner_max, kv2, k0sq, eshift, V);
   return cudaGetLastError();
 }
 

@@ -21,6 +21,7 @@
 #include <string>
 
 #include "../../include/cbs.h"
+#include "absorber.h"
 
 namespace cbs {
 const char* set_last_error(const char* msg);   // api.cu
@@ -51,20 +52,10 @@ static __device__ __align__(256) Scratch g_scratch;
 struct LayerArgs {
   int n[3], lo[3], hi[3];
   double smax_lo[3], smax_hi[3];  // sigma_max of each face (0 where there is no layer)
+  double power;                   // ramp exponent
+  int corner_max;                 // overlapping layers: 0 add, 1 the largest
   double kv2;                     // (k_vac pitch)^2
 };
-
-__device__ __forceinline__ double axis_sigma(int i, int n, int lo, int hi, double slo, double shi) {
-  if (i < lo) {
-    const double t = (double)(lo - i) / lo;
-    return slo * t * t;
-  }
-  if (i >= n - hi) {
-    const double t = (double)(i - (n - hi - 1)) / hi;
-    return shi * t * t;
-  }
-  return 0.0;
-}
 
 template <class T, class Op>
 __device__ __forceinline__ T block_reduce(T v, Op op, T* sh) {
@@ -139,11 +130,11 @@ __global__ void k_noalloc_maxdev(const float* __restrict__ eps, long long N, Lay
     const int x = (int)(i - row * L.n[0]);
     const int z = (int)(row / L.n[1]);
     const int y = (int)(row - (long long)z * L.n[1]);
-    const double sx = axis_sigma(x, L.n[0], L.lo[0], L.hi[0], L.smax_lo[0], L.smax_hi[0]);
-    const double sy = axis_sigma(y, L.n[1], L.lo[1], L.hi[1], L.smax_lo[1], L.smax_hi[1]);
-    const double sz = axis_sigma(z, L.n[2], L.lo[2], L.hi[2], L.smax_lo[2], L.smax_hi[2]);
+    const double sx = cbs::layer_axis_sigma(x, L.n[0], L.lo[0], L.hi[0], L.smax_lo[0], L.smax_hi[0], L.power);
+    const double sy = cbs::layer_axis_sigma(y, L.n[1], L.lo[1], L.hi[1], L.smax_lo[1], L.smax_hi[1], L.power);
+    const double sz = cbs::layer_axis_sigma(z, L.n[2], L.lo[2], L.hi[2], L.smax_lo[2], L.smax_hi[2], L.power);
     const double re = L.kv2 * (double)eps[i] - k0sq;
-    const double im = L.kv2 * (sx + sy + sz);
+    const double im = L.kv2 * cbs::layer_combine(sx, sy, sz, L.corner_max);
     m = fmax(m, sqrt(re * re + im * im));
   }
   m = block_reduce(m, [](double p, double q) { return fmax(p, q); }, sh);
@@ -203,6 +194,10 @@ extern "C" int cbs_splitting_noalloc(const cbs_plan_desc* d, const float* eps_re
   }
   if (!(d->pitch_m > 0) || !(d->lambda_m > 0) || !(d->n_bg > 0))
     return err(CBS_ERR_ARG, "pitch, wavelength and n_bg must be positive");
+  const cbs::LayerSpec layers = cbs::layer_spec(d->layer_round_trip, d->layer_power, d->layer_corner_max);
+  if (!cbs::layer_spec_valid(layers))
+    return err(CBS_ERR_ARG, "layer round trip %g, power %g or corner rule %d out of range", d->layer_round_trip,
+               d->layer_power, d->layer_corner_max);
   const long long N = (long long)d->nx * d->ny * d->nz;
   const long long blocks = (N + kVoxelsPerBlock - 1) / kVoxelsPerBlock;
   if (blocks > kMaxBlocks)
@@ -222,10 +217,11 @@ extern "C" int cbs_splitting_noalloc(const cbs_plan_desc* d, const float* eps_re
     L.n[a] = dims[a];
     L.lo[a] = d->pad_lo[a];
     L.hi[a] = d->pad_hi[a];
-    // sigma_max = 3 n_bg ln(1e4) / (k_vac L pitch): round-trip amplitude 1e-4 through the layer
-    L.smax_lo[a] = d->pad_lo[a] ? 3.0 * d->n_bg * std::log(1.0e4) / (kvac * d->pad_lo[a] * d->pitch_m) : 0.0;
-    L.smax_hi[a] = d->pad_hi[a] ? 3.0 * d->n_bg * std::log(1.0e4) / (kvac * d->pad_hi[a] * d->pitch_m) : 0.0;
+    L.smax_lo[a] = cbs::layer_sigma_max(layers, d->n_bg, kvac, d->pad_lo[a], d->pitch_m);
+    L.smax_hi[a] = cbs::layer_sigma_max(layers, d->n_bg, kvac, d->pad_hi[a], d->pitch_m);
   }
+  L.power = layers.power;
+  L.corner_max = layers.corner_max;
   L.kv2 = (kvac * d->pitch_m) * (kvac * d->pitch_m);
 
   cudaStream_t st = static_cast<cudaStream_t>(d->cuda_stream);

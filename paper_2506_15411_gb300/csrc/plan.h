@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/cbs.h"
+#include "absorber.h"
 #include "cbs_internal.h"
 
 namespace cbs {
@@ -65,13 +66,16 @@ struct cbs_plan_s {
   cbs::IterArgs base{};
   size_t N = 0;
   double pitch = 0, kvac = 0;
+  cbs::LayerSpec layers{};         // absorbing-layer profile (absorber.h)
   int sms = 0;
   // device memory owned by the plan
   float2* V = nullptr;
   float2* W = nullptr;
   float2* Ei = nullptr;            // the field being iterated, padded rows
-  float2* tw = nullptr;
+  float2* tw = nullptr;             // per-stage twiddles of the three axes
+  float2* pq = nullptr;             // wave numbers of the spectrum positions of the three axes
   int4* stages = nullptr;
+  std::vector<int> radix_order[3];  // DIF radix order of each axis
   double* partials = nullptr;
   unsigned* counter = nullptr;
   double* hist = nullptr;

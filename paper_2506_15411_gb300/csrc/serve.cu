@@ -42,14 +42,18 @@ struct ShapeKey {
   int nx, ny, nz;
   double pitch, lam, nbg;
   int lo[3], hi[3];
+  double layer_rt, layer_pow;
+  int layer_corner;
   bool operator==(const ShapeKey& o) const {
     return nx == o.nx && ny == o.ny && nz == o.nz && pitch == o.pitch && lam == o.lam && nbg == o.nbg &&
-           std::memcmp(lo, o.lo, sizeof(lo)) == 0 && std::memcmp(hi, o.hi, sizeof(hi)) == 0;
+           std::memcmp(lo, o.lo, sizeof(lo)) == 0 && std::memcmp(hi, o.hi, sizeof(hi)) == 0 &&
+           layer_rt == o.layer_rt && layer_pow == o.layer_pow && layer_corner == o.layer_corner;
   }
 };
 
 ShapeKey key_of(const cbs_request& r) {
-  ShapeKey k{r.nx, r.ny, r.nz, r.pitch_m, r.lambda_m, r.n_bg, {}, {}};
+  ShapeKey k{r.nx, r.ny, r.nz, r.pitch_m, r.lambda_m, r.n_bg, {}, {},
+             r.layer_round_trip, r.layer_power, r.layer_corner_max};
   for (int i = 0; i < 3; ++i) {
     k.lo[i] = r.pad_lo[i];
     k.hi[i] = r.pad_hi[i];
@@ -174,6 +178,9 @@ int make_slot(cbs_server_s* S, const ShapeKey& k, Slot** out) {
     pd.pad_lo[i] = k.lo[i];
     pd.pad_hi[i] = k.hi[i];
   }
+  pd.layer_round_trip = k.layer_rt;
+  pd.layer_power = k.layer_pow;
+  pd.layer_corner_max = k.layer_corner;
   pd.tol = S->d.tol;
   pd.max_iter = S->d.max_iter;
   pd.check_every = S->d.check_every;

@@ -1,21 +1,27 @@
 // xpass.cu -- the passes along x (contiguous rows) of the CBS iterations.
 //
 //   forward:  W_c = FFT_x(V E_c + S_c)                       (scattering potential and source
-//                                                              applied as the first FFT stage
+//                                                              formed as the first FFT stage
 //                                                              loads each element)
 //   inverse + next forward (one kernel):
 //             W_c = IFFT_x(W_c);  delta_c = gamma (E_c - W_c);  E_c -= delta_c;
-//             sum |delta|^2 in FP64, the update applied as the last inverse stage produces
-//             each element (update of the preconditioned series, refs. [25], [26] of
-//             arXiv 2506.15411); then W_c = FFT_x(V E_c + S_c) of the next iteration from
+//             sum |delta|^2 in FP64 (the update of the preconditioned series, refs. [25], [26]
+//             of arXiv 2506.15411); then W_c = FFT_x(V E_c + S_c) of the next iteration from
 //             the E just updated, while the tile is still on chip
+// The forward transforms are in-place decimation in frequency (the x spectrum stays in
+// digit-reversed order in W), the inverse ones decimation in time (fft_ip.cuh).  In the fused
+// kernel the last inverse stage, the update and the first forward stage of the next iteration
+// work on the same butterfly's values in registers, so the updated field never waits for a
+// barrier before it is transformed again.
 // A block owns a tile of `rpb` consecutive rows (z, y) of all three components.  Its rows are
 // contiguous in the padded layouts of E, V and W (row pitch nxp, 16 complex values), so the
 // tile arrives with one bulk copy (cp.async.bulk) per array and component and leaves the same
-// way; the transforms run in shared memory with the ping-pong Stockham engine.
+// way.  A block is persistent and keeps nset buffer sets: while it works on tile i, the copies
+// of tiles i+1 .. i+nset-1 are in flight.
 #include <algorithm>
 
-#include "stockham.cuh"
+#include "cbs_internal.h"
+#include "fft_ip.cuh"
 #include "tma.cuh"
 
 namespace cbs {
@@ -73,185 +79,211 @@ __device__ __forceinline__ void residual_finish(float acc, const IterArgs& a, do
 
 constexpr int kThreads = 512;
 
-// Shared-memory layout of a pipelined x kernel: two buffer sets, each [3][rpb][nxp] of the
-// input (E forward, W inverse), [3][rpb][nxp] of E (inverse only), [rpb][nxp] of V and, in
-// the forward kernel, its own scratch [3][rpb][nxp] (an odd number of FFT stages leaves the
-// result there, to be stored while the other set computes); then the inverse kernel's shared
-// scratch, the x twiddles, two mbarriers, flags and warp sums.
+// Shared-memory layout of an x kernel: nset buffer sets, each NARR arrays of [rpb][nxp]
+// (inverse kernel: W of 3 components, E of 3, V; forward kernel: E of 3 -- transformed in
+// place into W -- and V), then the x twiddles, nset mbarriers, flags and warp sums.
 struct XTile {
-  float2* in0;      // buffer set 0; set 1 starts `set` elements later
-  float2* e0;
-  float2* v0;
-  int set;
-  float2* scr;
+  float2* set0;
+  int set;          // elements per buffer set
   float2* tw;
-  uint64_t* full;   // [2]
+  uint64_t* full;   // [nset]
   int* fail;
   int* last;
   double* wsum;
 };
 
-__device__ __forceinline__ XTile carve(unsigned char* base, int rpb, int nxp, int twb, bool inverse) {
+__device__ __forceinline__ XTile carve(unsigned char* base, int rpb, int nxp, int twb, int nset, int narr) {
   const int span = rpb * nxp;
   float2* p = reinterpret_cast<float2*>(base);
   XTile t;
-  t.set = 7 * span;
-  t.in0 = p;
-  t.e0 = inverse ? p + 3 * span : nullptr;
-  t.v0 = p + (inverse ? 6 : 3) * span;
-  p += 2 * t.set;
-  if (inverse) {
-    t.scr = p;            // shared by both sets
-    p += 3 * span;
-  } else {
-    t.scr = t.v0 + span;  // set 0's scratch; set k's is t.scr + k * t.set
-  }
+  t.set0 = p;
+  t.set = narr * span;
+  p += nset * t.set;
   t.tw = p;
   p += twb / sizeof(float2);
   t.full = reinterpret_cast<uint64_t*>(p);
-  t.fail = reinterpret_cast<int*>(t.full + 2);
+  t.fail = reinterpret_cast<int*>(t.full + nset);
   t.last = t.fail + 1;
-  t.wsum = reinterpret_cast<double*>(t.full + 3);
+  t.wsum = reinterpret_cast<double*>(t.full + nset + 1);
   return t;
 }
 
 __device__ __forceinline__ int x_tiles(const IterArgs& a) { return (a.ny * a.nz + a.rpb - 1) / a.rpb; }
 
-// Persistent, double-buffered forward x pass: tile i is transformed in one buffer set while
-// the bulk copies of tile i+1 land in the other (issued after the first FFT stage, once the
-// store of tile i-1 from that set has left shared memory), and the store of tile i drains
-// during the next tile.
+// Row stages q0 .. q1-1 (forward) or q1-1 .. q0 (inverse) on ncomp x nr rows, a barrier after
+// each; `after_first` runs after the first barrier.
+template <bool INV, class Hook>
+__device__ __forceinline__ void row_stages(float2* buf, int cs, int ld, int nr, const AxisIP& ap, int q0, int q1,
+                                           const float2* tw, int tid, int nth, Hook after_first) {
+  const int ns = ap.ns;
+  for (int i = 0; i < q1 - q0; ++i) {
+    const int q = INV ? q1 - 1 - i : q0 + i;
+    const IPStage s = ip_decode_stage(ap, q);
+    radix_dispatch<16>(s.R, [&](auto Ri) {
+      constexpr int R = decltype(Ri)::value;
+      if (q < ns - 1)
+        ipr_stage<R, INV, true>(buf, cs, ld, nr, 3, s, tw, tid, nth);
+      else
+        ipr_stage<R, INV, false>(buf, cs, ld, nr, 3, s, tw, tid, nth);
+    });
+    __syncthreads();
+    if (i == 0) after_first();
+  }
+}
+
+// Persistent forward x pass (a series' first iteration): V E + S formed as the first stage
+// loads each element, transformed in place in the E buffer, stored as W.
 __global__ void __launch_bounds__(kThreads, 1) k_xpass_fwd(const IterArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int rpb = a.rpb, nxp = a.nxp;
+  const int rpb = a.rpb, nxp = a.nxp, nset = a.nset_xf;
   const int span = rpb * nxp;
   const int rows = a.ny * a.nz, ntiles = x_tiles(a);
-  XTile t = carve(smem_raw, rpb, nxp, a.twbx, false);
-  int tile = blockIdx.x;
-  if (tile >= ntiles) return;
-  if (!block_setup_n(t.in0, t.full, 2, t.fail, a.err)) return;
+  XTile t = carve(smem_raw, rpb, nxp, a.twbx, nset, 4);
+  if ((int)blockIdx.x >= ntiles) return;
+  if (!block_setup_n(t.set0, t.full, nset, t.fail, a.err)) return;
   const int tid = threadIdx.x, nth = blockDim.x;
+  const int G = gridDim.x;
   const float inv_ny = 1.0f / (float)a.ny;
   auto issue = [&](int tt, int k, uint32_t extra) {
     const int r0 = tt * rpb, nr = min(rpb, rows - r0);
     const uint32_t bytes = (uint32_t)(nr * nxp * sizeof(float2));
+    float2* s = t.set0 + k * t.set;
     mbar_arrive_expect_tx(&t.full[k], 4 * bytes + extra);
-    for (int c = 0; c < 3; ++c) bulk_load(t.in0 + k * t.set + c * span, a.E + c * a.Nw + (size_t)r0 * nxp, bytes, &t.full[k]);
-    bulk_load(t.v0 + k * t.set, a.V + (size_t)r0 * nxp, bytes, &t.full[k]);
+    for (int c = 0; c < 3; ++c) bulk_load(s + c * span, a.E + c * a.Nw + (size_t)r0 * nxp, bytes, &t.full[k]);
+    bulk_load(s + 3 * span, a.V + (size_t)r0 * nxp, bytes, &t.full[k]);
   };
   if (tid == 0) {
-    issue(tile, 0, a.twbx);
+    issue(blockIdx.x, 0, a.twbx);
     bulk_load(t.tw, a.twx, a.twbx, &t.full[0]);
+    for (int d = 1; d < nset - 1; ++d)
+      if ((int)blockIdx.x + d * G < ntiles) issue(blockIdx.x + d * G, d, 0);
   }
-  for (int i = 0; tile < ntiles; ++i, tile += gridDim.x) {
-    const int k = i & 1;
+  const int ns = a.ax.ns;
+  const IPStage s0 = ip_decode_stage(a.ax, 0);
+  int k = 0;
+  for (int i = 0, tile = blockIdx.x; tile < ntiles; ++i, tile += G, k = (k + 1 == nset) ? 0 : k + 1) {
     const int r0 = tile * rpb, nr = min(rpb, rows - r0);
-    const int tn = tile + gridDim.x;
-    if (!block_wait(&t.full[k], t.fail, a.err, (uint32_t)((i >> 1) & 1))) return;
-    float2* in = t.in0 + k * t.set;
-    const float2* v = t.v0 + k * t.set;
-    // V E + S, formed as the first FFT stage loads each element
-    auto pre = [&](int c, int row, int x, float2 e) {
-      const int gr = r0 + row;
-      const int z = fdiv(gr, inv_ny), y = gr - z * a.ny;
-      return cadd(cmul(v[row * nxp + x], e), source_at(a, c, z, y, x));
-    };
+    if (!block_wait(&t.full[k], t.fail, a.err, (uint32_t)((i / nset) & 1))) return;
+    float2* e = t.set0 + k * t.set;
+    const float2* v = e + 3 * span;
     auto prefetch = [&] {
+      const int tn = tile + (nset - 1) * G;
       if (tid == 0 && tn < ntiles) {
-        bulk_wait_read_all();   // the store of tile i-1 (from set k^1) has left shared memory
-        issue(tn, k ^ 1, 0);
+        bulk_wait_read_all();   // the store of tile i - 1 has left its buffer set
+        issue(tn, k == 0 ? nset - 1 : k - 1, 0);
       }
     };
-    const float2* w = fft_rows<false>(in, t.scr + k * t.set, nr, 3, nxp, span, a.ax, t.tw, tid, nth, pre, NoPost{},
-                                      prefetch);
+    auto gen = [&](int c, int row, int x, float2 ev) {
+      const int gr = r0 + row;
+      const int z = ip_div(gr, inv_ny), y = gr - z * a.ny;
+      return cadd(cmul(v[row * nxp + x], ev), source_at(a, c, z, y, x));
+    };
+    radix_dispatch<16>(s0.R, [&](auto Ri) {
+      constexpr int R = decltype(Ri)::value;
+      if (ns > 1)
+        ipr_dif_first<R, true>(e, span, nxp, nr, 3, s0, t.tw, tid, nth, gen);
+      else
+        ipr_dif_first<R, false>(e, span, nxp, nr, 3, s0, t.tw, tid, nth, gen);
+    });
+    __syncthreads();
+    prefetch();
+    row_stages<false>(e, span, nxp, nr, a.ax, 1, ns, t.tw, tid, nth, NoHookIP{});
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {
       const uint32_t bytes = (uint32_t)(nr * nxp * sizeof(float2));
-      for (int c = 0; c < 3; ++c) bulk_store(a.W + c * a.Nw + (size_t)r0 * nxp, w + c * span, bytes);
+      for (int c = 0; c < 3; ++c) bulk_store(a.W + c * a.Nw + (size_t)r0 * nxp, e + c * span, bytes);
       bulk_commit();
     }
   }
   if (tid == 0) bulk_wait_all();
 }
 
-// Persistent, double-buffered x pass that ends one iteration and starts the next on each
-// tile: the inverse x transform with the update and the FP64 residual, the store of E, then
-// the forward x transform of V E + S of the next iteration (formed from the updated E as its
-// first stage computes its inputs) and the store of W.  The series' first iteration runs
+// Persistent x pass that ends one iteration and starts the next on each tile: the inverse x
+// stages s-1 .. 1, then (fused, in registers) the last inverse stage, the update with the
+// FP64 residual and the first forward stage of V E + S of the next iteration, the store of E,
+// the forward stages 1 .. s-1 and the store of W.  The series' first iteration runs
 // k_xpass_fwd before it; after the last one the W it leaves is not used.
 __global__ void __launch_bounds__(kThreads, 1) k_xpass_inv_fwd(const IterArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int rpb = a.rpb, nxp = a.nxp;
+  const int rpb = a.rpb, nxp = a.nxp, nset = a.nset_x;
   const int span = rpb * nxp;
   const int rows = a.ny * a.nz, ntiles = x_tiles(a);
-  XTile t = carve(smem_raw, rpb, nxp, a.twbx, true);
-  int tile = blockIdx.x;
+  XTile t = carve(smem_raw, rpb, nxp, a.twbx, nset, 7);
   float acc = 0.f;
   const int tid = threadIdx.x, nth = blockDim.x;
-  if (tile < ntiles) {
-    if (!block_setup_n(t.in0, t.full, 2, t.fail, a.err)) return;
+  const int G = gridDim.x;
+  if ((int)blockIdx.x < ntiles) {
+    if (!block_setup_n(t.set0, t.full, nset, t.fail, a.err)) return;
     auto issue = [&](int tt, int k, uint32_t extra) {
       const int r0 = tt * rpb, nr = min(rpb, rows - r0);
       const uint32_t bytes = (uint32_t)(nr * nxp * sizeof(float2));
+      float2* s = t.set0 + k * t.set;
       mbar_arrive_expect_tx(&t.full[k], 7 * bytes + extra);
       for (int c = 0; c < 3; ++c) {
-        bulk_load(t.in0 + k * t.set + c * span, a.W + c * a.Nw + (size_t)r0 * nxp, bytes, &t.full[k]);
-        bulk_load(t.e0 + k * t.set + c * span, a.E + c * a.Nw + (size_t)r0 * nxp, bytes, &t.full[k]);
+        bulk_load(s + c * span, a.W + c * a.Nw + (size_t)r0 * nxp, bytes, &t.full[k]);
+        bulk_load(s + (3 + c) * span, a.E + c * a.Nw + (size_t)r0 * nxp, bytes, &t.full[k]);
       }
-      bulk_load(t.v0 + k * t.set, a.V + (size_t)r0 * nxp, bytes, &t.full[k]);
+      bulk_load(s + 6 * span, a.V + (size_t)r0 * nxp, bytes, &t.full[k]);
     };
     if (tid == 0) {
-      issue(tile, 0, a.twbx);
+      issue(blockIdx.x, 0, a.twbx);
       bulk_load(t.tw, a.twx, a.twbx, &t.full[0]);
+      for (int d = 1; d < nset - 1; ++d)
+        if ((int)blockIdx.x + d * G < ntiles) issue(blockIdx.x + d * G, d, 0);
     }
     const float ie = a.inv_eps;
     const float inv_ny = 1.0f / (float)a.ny;
-    // the forward transform's ping-pong buffers, ordered so that its result lands in the
-    // tile's W buffer (an odd number of stages >= 3 ends in the second one)
-    const bool res_in_b = (a.ax.ns % 2 == 1) && a.ax.ns >= 3;
-    for (int i = 0; tile < ntiles; ++i, tile += gridDim.x) {
-      const int k = i & 1;
+    const int ns = a.ax.ns;
+    const IPStage s0 = ip_decode_stage(a.ax, 0);
+    int k = 0;
+    for (int i = 0, tile = blockIdx.x; tile < ntiles; ++i, tile += G, k = (k + 1 == nset) ? 0 : k + 1) {
       const int r0 = tile * rpb, nr = min(rpb, rows - r0);
-      const int tn = tile + gridDim.x;
-      if (!block_wait(&t.full[k], t.fail, a.err, (uint32_t)((i >> 1) & 1))) return;
+      if (!block_wait(&t.full[k], t.fail, a.err, (uint32_t)((i / nset) & 1))) return;
+      float2* w = t.set0 + k * t.set;
+      float2* e = w + 3 * span;
+      const float2* v = w + 6 * span;
       auto prefetch = [&] {
+        const int tn = tile + (nset - 1) * G;
         if (tid == 0 && tn < ntiles) {
-          bulk_wait_read_all();   // the store of tile i-1 (from set k^1) has left shared memory
-          issue(tn, k ^ 1, 0);
+          bulk_wait_read_all();   // the stores of tile i - 1 have left its buffer set
+          issue(tn, k == 0 ? nset - 1 : k - 1, 0);
         }
       };
-      float2* e = t.e0 + k * t.set;
-      const float2* v = t.v0 + k * t.set;
-      // the update, applied as the last inverse-FFT stage produces each W element:
-      // delta = gamma (E - W), gamma = (i / epsilon) V; E -= delta; acc += |delta|^2
-      auto post = [&](int c, int row, int x, float2 w) {
+      row_stages<true>(w, span, nxp, nr, a.ax, 1, ns, t.tw, tid, nth, prefetch);
+      // the update at each natural-order element of the inverse transform, then the input of
+      // the next forward transform there:
+      //   delta = gamma (E - W), gamma = (i / epsilon) V;  E -= delta;  acc += |delta|^2;
+      //   returns V E + S
+      auto f = [&](int c, int row, int x, float2 wv) {
         const int o = row * nxp + x;
         const float2 vv = v[o];
         const float2 g = make_float2(-vv.y * ie, vv.x * ie);
         const float2 ec = e[c * span + o];
-        const float2 d = cmul(g, csub(ec, w));
-        e[c * span + o] = csub(ec, d);
+        const float2 d = cmul(g, csub(ec, wv));
+        const float2 en = csub(ec, d);
+        e[c * span + o] = en;
         acc = fmaf(d.x, d.x, fmaf(d.y, d.y, acc));
+        const int gr = r0 + row;
+        const int z = ip_div(gr, inv_ny), y = gr - z * a.ny;
+        return cadd(cmul(vv, en), source_at(a, c, z, y, x));
       };
-      float2* win = t.in0 + k * t.set;
-      fft_rows<true>(win, t.scr, nr, 3, nxp, span, a.ax, t.tw, tid, nth, NoPre{}, post, prefetch);
+      radix_dispatch<16>(s0.R, [&](auto Ri) {
+        constexpr int R = decltype(Ri)::value;
+        if (ns > 1)
+          ipx_fused<R, true>(w, span, nxp, nr, 3, s0, t.tw, tid, nth, f);
+        else
+          ipx_fused<R, false>(w, span, nxp, nr, 3, s0, t.tw, tid, nth, f);
+      });
       fence_async_smem();
       __syncthreads();
+      if (ns == 1) prefetch();
       const uint32_t bytes = (uint32_t)(nr * nxp * sizeof(float2));
       if (tid == 0) {
         for (int c = 0; c < 3; ++c) bulk_store(a.E + c * a.Nw + (size_t)r0 * nxp, e + c * span, bytes);
         bulk_commit();
       }
-      // next iteration: W = FFT_x(V E + S) from the updated E (read while its store drains)
-      auto gen = generate([&](int c, int row, int x) {
-        const int gr = r0 + row;
-        const int z = fdiv(gr, inv_ny), y = gr - z * a.ny;
-        const int o = row * nxp + x;
-        return cadd(cmul(v[o], e[c * span + o]), source_at(a, c, z, y, x));
-      });
-      const float2* w = fft_rows<false>(res_in_b ? t.scr : win, res_in_b ? win : t.scr, nr, 3, nxp, span, a.ax,
-                                        t.tw, tid, nth, gen, NoPost{});
+      row_stages<false>(w, span, nxp, nr, a.ax, 1, ns, t.tw, tid, nth, NoHookIP{});
       fence_async_smem();
       __syncthreads();
       if (tid == 0) {
@@ -266,13 +298,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_xpass_inv_fwd(const IterArgs a)
 
 }  // namespace
 
-// two buffer sets, scratch, twiddles, then 16 (two mbarriers) + 8 (two flags) + 32 * 8
+// nset buffer sets of NARR arrays, twiddles, then nset mbarriers + 8 (two flags) + 32 * 8
 // (warp sums) bytes
 size_t xpass_smem(const IterArgs& a) {
-  return (size_t)17 * a.rpb * a.nxp * sizeof(float2) + a.twbx + 24 + 32 * 8;
+  return (size_t)7 * a.nset_x * a.rpb * a.nxp * sizeof(float2) + a.twbx + 8 * a.nset_x + 8 + 32 * 8;
 }
 size_t xpass_fwd_smem(const IterArgs& a) {
-  return (size_t)14 * a.rpb * a.nxp * sizeof(float2) + a.twbx + 24 + 32 * 8;
+  return (size_t)4 * a.nset_xf * a.rpb * a.nxp * sizeof(float2) + a.twbx + 8 * a.nset_xf + 8 + 32 * 8;
 }
 int xpass_tiles(const IterArgs& a) { return (a.ny * a.nz + a.rpb - 1) / a.rpb; }
 

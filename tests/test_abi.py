@@ -50,6 +50,7 @@ int main(void) {
   printf("cbs_result size %zu\n", sizeof(cbs_result));
   F(cbs_plan_desc, pitch_m); F(cbs_plan_desc, pad_lo); F(cbs_plan_desc, pad_hi); F(cbs_plan_desc, tol);
   F(cbs_plan_desc, max_iter); F(cbs_plan_desc, check_every); F(cbs_plan_desc, cuda_stream);
+  F(cbs_plan_desc, layer_round_trip); F(cbs_plan_desc, layer_power); F(cbs_plan_desc, layer_corner_max);
   F(cbs_source, pol); F(cbs_source, z_plane); F(cbs_source, r0); F(cbs_source, user_src_dev);
   F(cbs_source, warm_start);
   F(cbs_stats, rel_resid); F(cbs_stats, resid0); F(cbs_stats, seconds); F(cbs_stats, status);
@@ -58,7 +59,8 @@ int main(void) {
   F(cbs_design_desc, beta1); F(cbs_design_desc, beta2); F(cbs_design_desc, adam_eps);
   F(cbs_server_desc, max_active); F(cbs_server_desc, tol); F(cbs_server_desc, max_iter);
   F(cbs_server_desc, check_every);
-  F(cbs_request, pitch_m); F(cbs_request, pad_lo); F(cbs_request, eps_host); F(cbs_request, eps_dev);
+  F(cbs_request, pitch_m); F(cbs_request, pad_lo); F(cbs_request, layer_round_trip);
+  F(cbs_request, layer_power); F(cbs_request, layer_corner_max); F(cbs_request, eps_host); F(cbs_request, eps_dev);
   F(cbs_request, src); F(cbs_request, adjoint); F(cbs_request, r0); F(cbs_request, E_host);
   F(cbs_request, E_dev); F(cbs_request, grad_host); F(cbs_request, grad_dev);
   F(cbs_result, status); F(cbs_result, objective); F(cbs_result, fwd); F(cbs_result, adj);
@@ -113,9 +115,10 @@ def test_plan_rejects_bad_descriptions_before_touching_the_device(built_lib):
     lib = L.load(built_lib)
     lam = 1.064e-6
 
-    def plan(nx=16, ny=16, nz=16, pitch=lam / 8, lo=(2, 2, 2), hi=(2, 2, 2), n_bg=1.0, max_iter=10, check_every=8):
+    def plan(nx=16, ny=16, nz=16, pitch=lam / 8, lo=(2, 2, 2), hi=(2, 2, 2), n_bg=1.0, max_iter=10, check_every=8,
+             rt=0.0, power=0.0, corner=0):
         d = L.cbs_plan_desc(nx, ny, nz, pitch, lam, n_bg, (ctypes.c_int * 3)(*lo), (ctypes.c_int * 3)(*hi),
-                            1e-4, max_iter, check_every, None)
+                            1e-4, max_iter, check_every, None, rt, power, corner)
         h = ctypes.c_void_p(1)
         rc = lib.cbs_plan(ctypes.byref(h), ctypes.byref(d))
         return rc, h.value, lib.cbs_last_error().decode()
@@ -124,7 +127,9 @@ def test_plan_rejects_bad_descriptions_before_touching_the_device(built_lib):
                       (dict(nx=17), "product"), (dict(nz=34), "product"), (dict(lo=(9, 2, 2)), "pads"),
                       (dict(hi=(2, 2, -1)), "pads"), (dict(lo=(8, 2, 2), hi=(8, 2, 2)), "pads"),
                       (dict(pitch=0.0), "positive"), (dict(n_bg=-1.0), "positive"),
-                      (dict(max_iter=0), ">= 1"), (dict(check_every=0), ">= 1")]:
+                      (dict(max_iter=0), ">= 1"), (dict(check_every=0), ">= 1"),
+                      (dict(rt=1.5), "layer"), (dict(rt=-0.1), "layer"), (dict(power=-1.0), "layer"),
+                      (dict(corner=2), "layer")]:
         rc, h, msg = plan(**kw)
         assert rc == L.CBS_ERR_ARG and h is None and words in msg, (kw, rc, msg)
     assert lib.cbs_plan(None, None) == L.CBS_ERR_ARG

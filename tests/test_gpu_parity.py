@@ -58,10 +58,12 @@ CASES = [
     (10, 9, 315, LAM / 16, (2, 2, 96), (2, 2, 96)),
     (32, 24, 1, LAM / 8, (4, 4, 0), (4, 4, 0)),
     (16, 13, 12, LAM / 8, (2, 2, 2), (2, 2, 2)),
-    # the longest axes: x and y at the 1024 limit, z at 704 (the z tiles bound nz)
+    # the longest axes: x and y at the 1024 limit, z at 704 and at 1001 = 7 * 11 * 13 (odd,
+    # three odd radices, boxes that do not divide the axis)
     (1024, 8, 6, LAM / 8, (8, 1, 1), (8, 1, 1)),
     (6, 1024, 8, LAM / 8, (1, 8, 1), (1, 8, 1)),
     (8, 6, 704, LAM / 8, (1, 1, 8), (1, 1, 8)),
+    (6, 8, 1001, LAM / 8, (1, 1, 8), (1, 1, 8)),
 ]
 
 
@@ -183,8 +185,8 @@ def test_argument_errors():
         CBSPlan(16, 16, 16, LAM / 8, LAM, pad_lo=(9, 0, 0))
     assert e.value.code == CBS_ERR_ARG
     with pytest.raises(CBSError) as e:
-        CBSPlan(16, 16, 715, LAM / 8, LAM)         # 5 * 11 * 13: its z tiles exceed shared memory
-    assert e.value.code == CBS_ERR_ARG and "too long" in str(e.value)
+        CBSPlan(16, 16, 2048, LAM / 8, LAM)        # beyond the 1024 limit of an axis
+    assert e.value.code == CBS_ERR_ARG
     with CBSPlan(16, 16, 16, LAM / 8, LAM, pad_lo=(2, 2, 2)) as plan:
         with pytest.raises(CBSError) as e:
             plan.forward(PlaneWave())

@@ -278,3 +278,56 @@ def test_absorption_maps_each_axis_profile_and_adds_them_in_edges_and_corners():
     assert np.isclose(at(16, 0, 3), want)
     # the strengths differ per width, so the checks above separate the axes
     assert len({round(S(g, L), 9) for L in (2, 3, 4, 5, 6, 7)}) == 6
+
+
+def _layer_reflection(ppl, layer_wl, round_trip, power, n_bg=1.0):
+    """|reflected / incident| amplitude of a plane wave hitting the high-z layer of a 1-voxel
+    column (nx = ny = 1: the problem is one-dimensional), fitted as A e^{ik_b z} + B e^{-ik_b z}
+    between the source sheet and the layer."""
+    L = int(round(layer_wl * ppl))
+    nz = 2 * L + 6 * ppl
+    g = co.Grid(1, 1, nz, LAM / ppl, LAM, n_bg, (0, 0, L), (0, 0, L), round_trip=round_trip, power=power)
+    eps = np.full(g.shape, n_bg ** 2)
+    zs = L + 2
+    r = co.forward(g, eps, co.plane_wave_source(g, z_plane=zs), tol=1e-11, max_iter=400000)
+    E = r.E[0, :, 0, 0]
+    z = np.arange(zs + ppl, nz - L - ppl)
+    kb = g.k_vac * n_bg
+    M = np.stack([np.exp(1j * kb * (z - zs) * g.pitch), np.exp(-1j * kb * (z - zs) * g.pitch)], 1)
+    A, B = np.linalg.lstsq(M, E[z], rcond=None)[0]
+    return abs(B / A), co.splitting(co.k_squared(g, eps)).epsilon / g.k_vac ** 2
+
+
+@pytest.mark.parametrize("round_trip,power,n_bg", [(1e-4, 2.0, 1.0), (1e-3, 3.0, 1.0), (1e-2, 2.0, 1.0),
+                                                   (1e-3, 2.0, 1.5)])
+def test_thick_layer_reflects_its_round_trip(round_trip, power, n_bg):
+    """A layer six wavelengths thick (the paper's z layers) reflects a normally incident plane
+    wave by about the round-trip amplitude its strength is set for: the reflection there is the
+    wave that crossed the layer, met the periodic wrap and came back, and the ramp is gentle
+    enough to reflect less.  This pins sigma_max = (p + 1) n_bg ln(1/round_trip) / (k_vac L) --
+    the exponent factor and the background index included -- to a measured quantity."""
+    refl, _ = _layer_reflection(8, 6, round_trip, power, n_bg)
+    assert 0.5 * round_trip <= refl <= 1.6 * round_trip, refl
+
+
+def test_thin_layer_reflection_and_the_gentler_setting():
+    """A layer one wavelength thick (the paper's x and y layers) reflects through its gradient
+    more than its round trip: about 5 % for the default 1e-4, while a 1e-2 layer reflects
+    less (under 3 %) and halves the series' shift epsilon."""
+    r_def, e_def = _layer_reflection(8, 1, 1e-4, 2.0)
+    r_gen, e_gen = _layer_reflection(8, 1, 1e-2, 2.0)
+    assert 0.02 <= r_def <= 0.07, r_def
+    assert r_gen <= 0.03 and r_gen < r_def, (r_gen, r_def)
+    assert abs(e_gen / e_def - 0.5) < 0.05, (e_gen, e_def)
+
+
+def test_corner_rule_max_takes_the_largest_profile():
+    g = co.Grid(20, 24, 28, LAM / 8, LAM, 1.0, (2, 3, 4), (5, 6, 7), corner="max")
+    sig = co.absorption(g)
+    S = co.layer_strength
+    want = max(S(g, 5) * (2 / 5) ** 2, S(g, 3) * (3 / 3) ** 2, S(g, 4) * (1 / 4) ** 2)
+    assert np.isclose(sig[3, 0, 16], want)
+    assert np.isclose(sig[27, 12, 0], max(S(g, 2), S(g, 7)))
+    assert np.isclose(sig[14, 12, 0], S(g, 2)) and sig[14, 12, 10] == 0.0
+    with pytest.raises(ValueError):
+        co.absorption(co.Grid(4, 4, 4, LAM / 8, LAM, 1.0, (1, 1, 1), (1, 1, 1), corner="mean"))
