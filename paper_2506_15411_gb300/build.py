@@ -21,7 +21,8 @@ LIBDIR = os.path.join(PKG, "lib")
 OBJDIR = os.path.join(LIBDIR, "_build")
 LIB = os.path.join(LIBDIR, "libcbs.so")
 
-SOURCES = ["api.cu", "xpass.cu", "yzpass.cu", "misc.cu", "noalloc.cu", "design.cu", "serve.cu"]
+SOURCES = ["api.cu", "xpass.cu", "yzpass.cu", "ypass_tx4.cu", "ypass_tx8.cu", "ypass_tx16.cu", "zpass_tx4.cu",
+           "zpass_tx8.cu", "zpass_tx16.cu", "misc.cu", "noalloc.cu", "design.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", CSRC, "-I", os.path.join(ROOT, "include")]

@@ -64,8 +64,28 @@ constexpr double kPiD = 3.14159265358979323846;
 constexpr int kMaxYZOcc = CBS_MAX_YZ_OCC;    // a build with 1 keeps every y/z kernel at one block per SM
 constexpr int kMinOcc2Tx = CBS_MIN_OCC2_TX;  // narrowest tile worth two blocks per SM
 constexpr int kYZMaxBuf = CBS_YZ_MAX_BUF;    // most tile buffers of a y or z block
+#ifndef CBS_YBLOCK
+#define CBS_YBLOCK 128
+#endif
+constexpr int kYBlock = CBS_YBLOCK;          // target rows of a y block of the plan's arrays
 constexpr int kXSets = CBS_X_SETS;           // most buffer sets of an x block ...
 constexpr int kXMinRows = CBS_X_MIN_ROWS;    // ... while its tiles keep at least this many rows
+#ifndef CBS_X_OCC
+#define CBS_X_OCC 1
+#endif
+#ifndef CBS_Z_OCC
+#define CBS_Z_OCC 1
+#endif
+#ifndef CBS_Z_GROUPS
+#define CBS_Z_GROUPS 2
+#endif
+#ifndef CBS_X_GROUPS
+#define CBS_X_GROUPS 2
+#endif
+constexpr int kXGroups = CBS_X_GROUPS;       // warp groups of the fused x block
+constexpr int kXOcc = CBS_X_OCC;             // x blocks per SM (the kernels' launch bounds)
+constexpr int kZOcc = CBS_Z_OCC;             // z blocks per SM
+constexpr int kZGroups = CBS_Z_GROUPS;       // warp groups of a z block
 constexpr int kMaxN = 1024;
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
@@ -85,18 +105,18 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// 4D map of the workspace W viewed as [3][nz][ny][nx] complex64 (8-byte elements) with row
-// pitch nxp; box = {bx, by, bz, 1}.  Elements beyond nx, ny or nz read as zero and are not
-// written.
-bool encode_w_map(CUtensorMap* tm, float2* W, int nx, int ny, int nz, int nxp, int bx, int by, int bz) {
+// 5D map of the workspace W in its y-blocked layout, viewed as [3][nyb][nz][yblk][nx]
+// complex64 (8-byte elements) with row pitch nxp; box = {bx, by, bz, 1, 1} over (x, y in
+// block, z).  Elements beyond nx or nz read as zero and are not written.
+bool encode_w_map(CUtensorMap* tm, float2* W, int nx, int ny, int nz, int nxp, int yblk, int bx, int by, int bz) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
-  const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, 3};
+  const cuuint64_t dims[5] = {(cuuint64_t)nx, (cuuint64_t)yblk, (cuuint64_t)nz, (cuuint64_t)(ny / yblk), 3};
   const cuuint64_t row = (cuuint64_t)nxp * sizeof(float2);
-  const cuuint64_t strides[3] = {row, row * ny, row * ny * nz};
-  const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1};
-  const cuuint32_t estr[4] = {1, 1, 1, 1};
-  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, W, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  const cuuint64_t strides[4] = {row, row * yblk, row * yblk * nz, row * ny * nz};
+  const cuuint32_t box[5] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, W, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -257,9 +277,13 @@ int make_source(cbs_plan_s* p, const cbs_source* src, SourceArgs& s) {
 }
 
 
-size_t dense_row_bytes(const cbs_plan_s* p) { return (size_t)p->d.nx * sizeof(float2); }
-size_t pad_row_bytes(const cbs_plan_s* p) { return (size_t)p->base.nxp * sizeof(float2); }
-size_t field_rows(const cbs_plan_s* p) { return (size_t)3 * p->d.ny * p->d.nz; }
+// Copy a field between the caller's dense layout [3][nz][ny][nx] and the plan's y-blocked
+// one (the row padding is never written here: it stays zero).
+cudaError_t field_copy(const cbs_plan_s* p, float2* dense, bool to_dense) {
+  const IterArgs& a = p->base;
+  return to_dense ? launch_field_layout(p->Ei, dense, true, a.nx, a.ny, a.nz, a.nxp, a.yblk, p->stream)
+                  : launch_field_layout(dense, p->Ei, false, a.nx, a.ny, a.nz, a.nxp, a.yblk, p->stream);
+}
 
 // Enqueue the next block of iterations, the copy of its residual sums and of the error flag,
 // and the event the host waits on.
@@ -329,8 +353,7 @@ bool series_absorb_block(cbs_plan_s* p, SeriesRun& R) {
 // Copy the iterate back into the caller's field (also after an error: E then holds the last
 // iterate), with blk_ev marking its end.
 void series_enqueue_copy_out(cbs_plan_s* p, SeriesRun& R) {
-  cudaError_t e = cudaMemcpy2DAsync(R.E, dense_row_bytes(p), p->Ei, pad_row_bytes(p), dense_row_bytes(p),
-                                    field_rows(p), cudaMemcpyDeviceToDevice, p->stream);
+  cudaError_t e = field_copy(p, R.E, true);
   if (e == cudaSuccess) e = cudaEventRecord(p->blk_ev, p->stream);
   if (e != cudaSuccess) {
     if (R.rc == CBS_OK) R.rc = fail(CBS_ERR_CUDA, "field copy-out: %s", cudaGetErrorString(e));
@@ -392,8 +415,7 @@ void series_begin(cbs_plan_s* p, float2* E, const SourceArgs& src, int warm, Ser
     e = cudaMemsetAsync(p->Ei, 0, 3 * R.a.Nw * sizeof(float2), p->stream);
   }
   if (warm && e == cudaSuccess)
-    e = cudaMemcpy2DAsync(p->Ei, pad_row_bytes(p), E, dense_row_bytes(p), dense_row_bytes(p), field_rows(p),
-                          cudaMemcpyDeviceToDevice, p->stream);
+    e = field_copy(p, E, false);
   if (e == cudaSuccess) e = launch_xpass_fwd(R.a, p->stream);   // W of the first iteration
   if (e != cudaSuccess) {
     R.rc = fail(CBS_ERR_CUDA, "field copy-in: %s", cudaGetErrorString(e));
@@ -557,6 +579,7 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
   // so a tile needs no scratch): x tiles of rpb rows, y and z tiles of TX columns by whole
   // tensor-copy boxes
   const size_t kBlockBudget = 220 * 1024, kBlockBudget2 = 110 * 1024;
+  const size_t kXBudget = kBlockBudget / kXOcc, kZBudget = kBlockBudget / kZOcc;
   a.nxp = round_up(d.nx, 16);
   a.Nw = (size_t)a.nxp * d.ny * d.nz;
   const int twb[3] = {round_up(d.nx * (int)sizeof(float2), 16), round_up(d.ny * (int)sizeof(float2), 16),
@@ -564,17 +587,18 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
   {
     // x: nset buffer sets of 7 arrays [rpb][nxp] (W and E of 3 components, V); the most sets
     // (up to kXSets) that still hold tiles of at least kXMinRows rows, then the most rows
-    const size_t fixed = (size_t)twb[0] + 8 * 4 + 8 + 32 * 8;
+    const size_t fixed = (size_t)twb[0] + 8 * 5 + 16 + 32 * 8;
     const size_t row7 = (size_t)7 * a.nxp * sizeof(float2);
-    a.nset_x = 2;
-    for (int ns = kXSets; ns >= 2; --ns)
-      if ((kBlockBudget - fixed) / (ns * row7) >= (size_t)kXMinRows || ns == 2) {
+    a.xgroups = kXGroups;
+    a.nset_x = kXGroups + 1;   // a tile in hand per warp group and one more in flight
+    for (int ns = std::max(kXSets, kXGroups + 1); ns >= kXGroups + 1; --ns)
+      if ((kXBudget - fixed) / (ns * row7) >= (size_t)kXMinRows || ns == kXGroups + 1) {
         a.nset_x = ns;
         break;
       }
-    a.rpb = (int)std::max<size_t>(1, std::min<size_t>(64, (kBlockBudget - fixed) / (a.nset_x * row7)));
+    a.rpb = (int)std::max<size_t>(1, std::min<size_t>(64, (kXBudget - fixed) / (a.nset_x * row7)));
     const size_t row4 = (size_t)4 * a.rpb * a.nxp * sizeof(float2);
-    a.nset_xf = (int)std::max<size_t>(2, std::min<size_t>(4, (kBlockBudget - fixed) / row4));
+    a.nset_xf = (int)std::max<size_t>(2, std::min<size_t>(4, (kXBudget - fixed) / row4));
   }
   // y and z tiles: TX columns x whole axis, brought in by boxes of B rows.  B is a divisor of
   // the axis in [16, 64] when one keeps every box's shared-memory offset (B TX 8 bytes) a
@@ -587,12 +611,23 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
     return kBoxRows;
   };
   const int pqbz = round_up(d.nz * (int)sizeof(float2), 16);
+  // y blocks of the arrays: the largest divisor of ny up to kYBlock rows whose tensor-copy box
+  // keeps the y tile's shared-memory offsets on 128-byte boundaries (yblk TX 8 bytes), else
+  // up to 256 rows (the box limit); 0 if none (then that tile width is not used)
+  auto yblock_for = [&](int tx) {
+    for (int lim : {kYBlock, 256})
+      for (int b = std::min(lim, d.ny); b >= 1; --b)
+        if (d.ny % b == 0 && (b * tx) % 16 == 0) return b;
+    return 0;
+  };
+  // a y tile holds exactly ny rows (nyb boxes of yblk rows)
   auto ysmem = [&](int tx, int nb) {
-    const int rows = round_up(d.ny, box_rows(d.ny, tx));
-    return (size_t)nb * rows * tx * sizeof(float2) + twb[1] + 8 * nb + 8;
+    if (!yblock_for(tx)) return (size_t)1 << 40;
+    return (size_t)nb * d.ny * tx * sizeof(float2) + twb[1] + 8 * nb + 8;
   };
   auto zsmem = [&](int tx, int nb) {
-    return (size_t)3 * nb * round_up(d.nz, box_rows(d.nz, tx)) * tx * sizeof(float2) + twb[2] + pqbz + 8 * nb + 8;
+    return (size_t)3 * nb * round_up(d.nz, box_rows(d.nz, tx)) * tx * sizeof(float2) + twb[2] + pqbz + 8 * (nb + 1) +
+           8;
   };
   auto max_radix = [](const std::vector<int>& r) { return *std::max_element(r.begin(), r.end()); };
   // Two blocks per SM (half the shared memory each) when the axis needs no radix above 11,
@@ -606,16 +641,30 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
     }
     return false;
   };
+  // z: every warp group needs a tile in hand and one more in flight; two groups while the
+  // tiles allow, else one
+  auto pick_z = [&](int& tx, int& nb, int& groups) {
+    for (groups = kZGroups; groups >= 1; --groups)
+      for (tx = 16; tx >= 4; tx /= 2)
+        for (nb = kYZMaxBuf; nb >= groups + 1; --nb)
+          if (zsmem(tx, nb) <= kZBudget) return true;
+    return false;
+  };
   const bool fy = pick(ysmem, max_radix(rad[1]), a.tx_y, a.nbuf_y, a.occ_y);
-  const bool fz = pick(zsmem, 16, a.tx_z, a.nbuf_z, a.occ_z);   // the z pass runs at one block per SM
+  const bool fz = pick_z(a.tx_z, a.nbuf_z, a.zgroups);
+  a.occ_z = kZOcc;
   if (!fy || !fz) {
     fail(CBS_ERR_ARG, "axis too long for the shared-memory tiles");
     return bail(CBS_ERR_ARG);
   }
-  a.yb = box_rows(d.ny, a.tx_y);
+  a.yblk = yblock_for(a.tx_y);
+  a.nyb = d.ny / a.yblk;
+  a.yb = a.yblk;
+  a.nyr = d.ny;
   a.zb = box_rows(d.nz, a.tx_z);
-  a.nyr = round_up(d.ny, a.yb);
   a.nzr = round_up(d.nz, a.zb);
+  a.maxr_x = max_radix(rad[0]);
+  a.maxr_z = max_radix(rad[2]);
   a.twbx = twb[0];
   a.twby = twb[1];
   a.twbz = twb[2];
@@ -630,8 +679,8 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
   CKP(cudaMalloc(&p->err_dev, sizeof(int)));
   CKP(cudaMemset(p->err_dev, 0, sizeof(int)));
   CKP(cudaMallocHost(&p->err_host, sizeof(int)));
-  if (!encode_w_map(&p->tmy, p->W, d.nx, d.ny, d.nz, a.nxp, a.tx_y, a.yb, 1) ||
-      !encode_w_map(&p->tmz, p->W, d.nx, d.ny, d.nz, a.nxp, a.tx_z, 1, a.zb)) {
+  if (!encode_w_map(&p->tmy, p->W, d.nx, d.ny, d.nz, a.nxp, a.yblk, a.tx_y, a.yblk, 1) ||
+      !encode_w_map(&p->tmz, p->W, d.nx, d.ny, d.nz, a.nxp, a.yblk, a.tx_z, 1, a.zb)) {
     fail(CBS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the workspace");
     return bail(CBS_ERR_CUDA);
   }
@@ -855,7 +904,7 @@ int cbs_set_permittivity(cbs_plan_t p, const float* eps) {
   for (int b = 0; b < B; ++b) epsilon = std::max(epsilon, dv[b]);
   if (!(epsilon > 0.0) || !std::isfinite(epsilon))
     return fail(CBS_ERR_ARG, "epsilon = %g: a lossless homogeneous grid has no convergent splitting", epsilon);
-  CK(launch_build_v(eps, p->d.nx, p->d.ny, p->d.nz, p->base.nxp, p->sx, p->sy, p->sz, p->layers.corner_max, kv2,
+  CK(launch_build_v(eps, p->d.nx, p->d.ny, p->d.nz, p->base.nxp, p->base.yblk, p->sx, p->sy, p->sz, p->layers.corner_max, kv2,
                     k0sq, epsilon, p->V, p->stream));
   CK(cudaStreamSynchronize(p->stream));
   p->k0sq_s = k0sq;

@@ -26,7 +26,8 @@ struct IterArgs {
   int nx, ny, nz;
   size_t N;               // nx * ny * nz (fields E, V, sources: dense rows)
   int nxp;                // row pitch of the workspace W (multiple of 16 complex values)
-  size_t Nw;              // nxp * ny * nz: component stride of W
+  int yblk, nyb;          // y-blocked layout: blocks of yblk y rows (yblk divides ny), nyb blocks
+  size_t Nw;              // nxp * ny * nz: component stride of W, E
   int yb, zb;             // rows per tensor-copy box along y and z
   int nyr, nzr;           // ny, nz rounded up to whole boxes (shared-memory rows of a tile)
   AxisIP ax, ay, az;      // in-place FFT plans (fft_ip.cuh)
@@ -38,9 +39,9 @@ struct IterArgs {
   const float2* pqy;      // padded with zeros to a multiple of 16 entries
   const float2* pqz;
   int pqbz;               // bytes of the z table the z pass copies (multiple of 16)
-  float2* E;              // field being iterated, [3][nz][ny][nxp] (plan-owned copy)
-  float2* W;              // workspace [3][nz][ny][nxp]
-  const float2* V;        // potential [nz][ny][nxp], scaled
+  float2* E;              // field being iterated, [3][nyb][nz][yblk][nxp] (plan-owned copy)
+  float2* W;              // workspace, same layout
+  const float2* V;        // potential [nyb][nz][yblk][nxp], scaled
   SourceArgs src;
   float inv_eps;          // 1 / epsilon (scaled)
   float2 kt2;             // k0^2 + i epsilon (scaled)
@@ -56,8 +57,20 @@ struct IterArgs {
   int tx_y, tx_z;         // x-columns per tile, y and z passes
   int nbuf_y, nbuf_z;     // tile buffers of the pipelined y and z passes (2 to 4)
   int occ_y, occ_z;       // blocks per SM of the y and z kernels (2: radices <= 11, 64 registers)
+  int maxr_x, maxr_z;     // largest radix of the x and z axes (selects the kernel build)
+  int xgroups, zgroups;   // warp groups of the fused x and the z blocks (1 or 2)
   int grid_x, grid_xf, grid_y, grid_z;   // persistent grid sizes (x inverse, x forward, y, z)
 };
+
+// The plan's arrays (W, the iterate E, V) store row (y, z) of a component at
+//     ((y / yblk) * nz + z) * yblk + y mod yblk
+// -- blocks of yblk consecutive y rows, z inside a block: a z column then visits rows yblk
+// rows apart (instead of ny), and a y column runs in nyb stretches of yblk rows.  Long
+// z strides of the plain [z][y] order slowed the z pass by half on a 640 x 640 plane.
+CBS_HD size_t wrow(int y, int z, int nz, int yblk) {
+  const int yb = y / yblk;
+  return ((size_t)yb * nz + z) * yblk + (y - yb * yblk);
+}
 
 // Launchers (one per pass of an iteration); each returns the launch error.
 cudaError_t launch_xpass_fwd(const IterArgs& a, cudaStream_t s);   // W = FFTx(V E + S)
@@ -67,8 +80,6 @@ cudaError_t launch_xpass_inv_fwd(const IterArgs& a, cudaStream_t s);  // IFFTx, 
 
 // Shared-memory bytes and threads of each pass for the plan's shapes.
 size_t xpass_smem(const IterArgs& a);
-size_t ypass_smem(const IterArgs& a);
-size_t zpass_smem(const IterArgs& a);
 int xpass_tiles(const IterArgs& a);
 cudaError_t yz_grid_sizes(IterArgs& a, int sms);   // sets grid_y, grid_z
 cudaError_t x_grid_size(IterArgs& a, int sms);     // sets grid_x, grid_xf
@@ -79,9 +90,13 @@ cudaError_t launch_eps_minmax(const float* eps, size_t N, float* part_min, float
 cudaError_t launch_k2_maxdev(const float* eps, int nx, int ny, int nz, const double* sx,
                              const double* sy, const double* sz, int corner_max, double kv2, double k0sq,
                              double* part, int blocks, cudaStream_t s);
-cudaError_t launch_build_v(const float* eps, int nx, int ny, int nz, int nxp, const double* sx,
+cudaError_t launch_build_v(const float* eps, int nx, int ny, int nz, int nxp, int yblk, const double* sx,
                            const double* sy, const double* sz, int corner_max, double kv2, double k0sq,
                            double eps_shift, float2* V, cudaStream_t s);
+// A field between the caller's dense layout [3][nz][ny][nx] and the plan's y-blocked one
+// (to_dense: plan -> dense); the row padding of the plan's copy is not written.
+cudaError_t launch_field_layout(const float2* src, float2* dst, bool to_dense, int nx, int ny, int nz, int nxp,
+                                int yblk, cudaStream_t s);
 cudaError_t launch_adjoint_amp(const float2* E, size_t N, int nx, int ny, int x, int y, int z,
                                float scale, float2* amp, cudaStream_t s);
 cudaError_t launch_gradient(const float2* E, const float2* Ea, size_t N, float coef, float* g,

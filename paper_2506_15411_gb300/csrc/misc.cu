@@ -76,8 +76,8 @@ __global__ void k_k2_maxdev(const float* __restrict__ eps, int nx, int ny, int n
   if (threadIdx.x == 0) part[blockIdx.x] = m;
 }
 
-// V in the padded row layout [nz][ny][nxp] of the iteration (the padding stays zero).
-__global__ void k_build_v(const float* __restrict__ eps, int nx, int ny, int nz, int nxp,
+// V in the y-blocked layout of the iteration (row padding stays zero).
+__global__ void k_build_v(const float* __restrict__ eps, int nx, int ny, int nz, int nxp, int yblk,
                           const double* __restrict__ sx, const double* __restrict__ sy,
                           const double* __restrict__ sz, int corner_max, double kv2, double k0sq,
                           double eshift, float2* __restrict__ V) {
@@ -87,7 +87,23 @@ __global__ void k_build_v(const float* __restrict__ eps, int nx, int ny, int nz,
     voxel_xyz(i, nx, ny, x, y, z);
     const double re = kv2 * (double)eps[i] - k0sq;
     const double im = kv2 * layer_combine(sx[x], sy[y], sz[z], corner_max) - eshift;
-    V[((size_t)z * ny + y) * nxp + x] = make_float2((float)re, (float)im);
+    V[wrow(y, z, nz, yblk) * nxp + x] = make_float2((float)re, (float)im);
+  }
+}
+
+// One thread per element of the 3 N field values, consecutive threads along x.
+__global__ void k_field_layout(const float2* __restrict__ src, float2* __restrict__ dst, int to_dense, int nx, int ny,
+                               int nz, int nxp, int yblk) {
+  const size_t N = (size_t)nx * ny * nz, Nw = (size_t)nxp * ny * nz;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < 3 * N; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t c = i / N, r = i - c * N;
+    int x, y, z;
+    voxel_xyz(r, nx, ny, x, y, z);
+    const size_t b = c * Nw + wrow(y, z, nz, yblk) * nxp + x;
+    if (to_dense)
+      dst[i] = src[b];
+    else
+      dst[b] = src[i];
   }
 }
 
@@ -159,10 +175,16 @@ cudaError_t launch_k2_maxdev(const float* eps, int nx, int ny, int nz, const dou
   return cudaGetLastError();
 }
 
-cudaError_t launch_build_v(const float* eps, int nx, int ny, int nz, int nxp, const double* sx,
+cudaError_t launch_build_v(const float* eps, int nx, int ny, int nz, int nxp, int yblk, const double* sx,
                            const double* sy, const double* sz, int corner_max, double kv2, double k0sq,
                            double eshift, float2* V, cudaStream_t s) {
-  k_build_v<<<152 * 8, 256, 0, s>>>(eps, nx, ny, nz, nxp, sx, sy, sz, corner_max, kv2, k0sq, eshift, V);
+  k_build_v<<<152 * 8, 256, 0, s>>>(eps, nx, ny, nz, nxp, yblk, sx, sy, sz, corner_max, kv2, k0sq, eshift, V);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_field_layout(const float2* src, float2* dst, bool to_dense, int nx, int ny, int nz, int nxp,
+                                int yblk, cudaStream_t s) {
+  k_field_layout<<<152 * 8, 256, 0, s>>>(src, dst, to_dense ? 1 : 0, nx, ny, nz, nxp, yblk);
   return cudaGetLastError();
 }
 

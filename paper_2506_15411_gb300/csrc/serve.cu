@@ -65,7 +65,7 @@ ShapeKey key_of(const cbs_request& r) {
 // reduction scratch under 16 MB) and the slot's eps, E, E_adj and gradient.
 size_t slot_bytes(const ShapeKey& k) {
   const size_t nxp = (size_t)((k.nx + 15) / 16 * 16);
-  const size_t Nw = nxp * k.ny * k.nz, N = (size_t)k.nx * k.ny * k.nz;
+  const size_t Nw = nxp * (k.ny + 1) * k.nz, N = (size_t)k.nx * k.ny * k.nz;   // planes may get a padding row
   return Nw * (8 + 24 + 24) + N * (4 + 24 + 24 + 4) + ((size_t)16 << 20);
 }
 

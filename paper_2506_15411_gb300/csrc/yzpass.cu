@@ -1,221 +1,20 @@
-// yzpass.cu -- the strided passes of one CBS iteration, fed by the Tensor Memory Accelerator.
-//
-//   y pass:  W_c <- FFT_y(W_c) or IFFT_y(W_c), one (component, z) plane x TX columns per tile
-//   z pass:  W <- IFFT_z( G(p) FFT_z(W) ), the three components of one y row x TX columns,
-//            where G(p) = (I - p p^T / kt2) / (|p|^2 - kt2), kt2 = k0^2 + i epsilon, is the
-//            dyadic Green's function of curl curl - kt2 (the vector CBS of refs. [25], [26] of
-//            arXiv 2506.15411), scaled by 1/N for the inverse FFT (Nyquist treatment at green()).
-//
-// Forward transforms are in-place decimation in frequency and leave each axis' spectrum in
-// digit-reversed order in W; inverse transforms are decimation in time and restore natural
-// order (fft_ip.cuh).  So the y rows the z pass sees are y frequencies in that order, and the
-// k-space multiply takes each position's wave number from the per-axis tables.  In the z pass
-// the last forward stage, the multiply and the first inverse stage run on the same values in
-// registers.
-//
-// A tile arrives by a few cp.async.bulk.tensor copies (boxes of TX columns x up to 64 rows;
-// rows past the end of an axis are zero-filled and never stored), is transformed in place in
-// shared memory and leaves by tensor stores.  A block is persistent and keeps nbuf tile
-// buffers: while it transforms tile i, the copies of tiles i+1 .. i+nbuf-1 are in flight.  The
-// workspace W has a padded row pitch (nxp, a multiple of 16 complex values) so that every
-// tensor stride is a multiple of 16 bytes and every box row starts on a 128-byte boundary.
+// yzpass.cu -- host side of the strided passes (y, and z with the k-space multiply): launch
+// shapes, grid sizes and launches.  The kernels are in yz_kernels.cuh and are compiled per
+// tile width in ypass_tx*.cu / zpass_tx*.cu.
 #include <algorithm>
 
-#include "cbs_internal.h"
-#include "fft_ip.cuh"
-#include "tma.cuh"
+#include "yz_kernels.cuh"
 
 namespace cbs {
 
+CBS_YZ_FUNCS(extern, 4)
+CBS_YZ_FUNCS(extern, 8)
+CBS_YZ_FUNCS(extern, 16)
+CBS_Z_FUNCS(extern, 4)
+CBS_Z_FUNCS(extern, 8)
+CBS_Z_FUNCS(extern, 16)
+
 namespace {
-
-// k-space multiply at wave vector p (q = p except 0 in a Nyquist component):
-//   X <- [X + q (q.X) / (|p|^2 - |q|^2 - kt2)] * invN / (|p|^2 - kt2),
-// the inverse of |p|^2 I - q q^T - kt2 I.  A Nyquist component (even axis length, wave number
-// pi/pitch whose sign is undefined) is 0 in q, which keeps the discrete curl curl real and
-// symmetric.  Away from Nyquist q = p and this is (I - p p^T / kt2) / (|p|^2 - kt2).
-__device__ __forceinline__ void green(float px, float py, float pz, float qx, float qy, float qz, float2 kt2,
-                                      float invN, float2& X0, float2& X1, float2& X2) {
-  const float p2 = px * px + py * py + pz * pz;
-  const float nyq2 = (px * px - qx * qx) + (py * py - qy * qy) + (pz * pz - qz * qz);
-  const float cr = nyq2 - kt2.x, ci = -kt2.y;
-  const float cs = __fdividef(1.0f, cr * cr + ci * ci);
-  const float2 qd = make_float2(qx * X0.x + qy * X1.x + qz * X2.x, qx * X0.y + qy * X1.y + qz * X2.y);
-  const float2 c = cmul(qd, make_float2(cr * cs, -ci * cs));
-  const float dr = p2 - kt2.x, di = -kt2.y;
-  const float sc = invN * __fdividef(1.0f, dr * dr + di * di);
-  const float2 inv = make_float2(dr * sc, -di * sc);   // invN / (dr + i di)
-  X0 = cmul(make_float2(X0.x + qx * c.x, X0.y + qx * c.y), inv);
-  X1 = cmul(make_float2(X1.x + qy * c.x, X1.y + qy * c.y), inv);
-  X2 = cmul(make_float2(X2.x + qz * c.x, X2.y + qz * c.y), inv);
-}
-
-constexpr int kYZThreads = 512;
-
-// Stages q0 .. q1-1 (forward) or q1-1 .. q0 (inverse) of column transforms of NCOMP x NCOL
-// columns held in `buf`, a barrier after each; `after_first` runs after the first barrier.
-// PAIRS: butterflies on column pairs (16-byte accesses) or, in the 64-register kernels, on
-// single columns.
-template <bool INV, int NCOL, int NCOMP, int MAXR, bool PAIRS, class Hook>
-__device__ __forceinline__ void col_stages(float2* buf, int cs, const AxisIP& ap, int q0, int q1, const float2* tw,
-                                           int tid, int nth, Hook after_first) {
-  const int ns = ap.ns;
-  for (int i = 0; i < q1 - q0; ++i) {
-    const int q = INV ? q1 - 1 - i : q0 + i;
-    const IPStage s = ip_decode_stage(ap, q);
-    radix_dispatch<MAXR>(s.R, [&](auto Ri) {
-      constexpr int R = decltype(Ri)::value;
-      if constexpr (PAIRS) {
-        if (q < ns - 1)
-          ipc_stage<R, INV, NCOL, NCOMP, true>(buf, cs, s, tw, tid, nth);
-        else
-          ipc_stage<R, INV, NCOL, NCOMP, false>(buf, cs, s, tw, tid, nth);
-      } else {
-        if (q < ns - 1)
-          ipc_stage1<R, INV, NCOL, NCOMP, true>(buf, cs, s, tw, tid, nth);
-        else
-          ipc_stage1<R, INV, NCOL, NCOMP, false>(buf, cs, s, tw, tid, nth);
-      }
-    });
-    __syncthreads();
-    if (i == 0) after_first();
-  }
-}
-
-// Persistent y pass: a block walks tiles t = blockIdx.x, + gridDim.x, ... through nbuf tile
-// buffers.  Tile i is transformed in buffer i mod nbuf; after its first stage, thread 0 issues
-// the copies of tile i + nbuf - 1 into the buffer of tile i - 1 (once that tile's store has
-// been read out of it).  OCC blocks per SM: 1 (up to 128 registers, all radices) or 2 (64
-// registers, radices up to MAXR = 11).
-template <int TX, bool INV, int OCC>
-__global__ void __launch_bounds__(kYZThreads, OCC) k_ypass(const __grid_constant__ CUtensorMap tm, const IterArgs a) {
-  constexpr int MAXR = OCC == 1 ? 16 : 11;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int tileN = a.nyr * TX, nbuf = a.nbuf_y;
-  float2* buf0 = reinterpret_cast<float2*>(smem_raw);   // nbuf x [nyr][TX]
-  float2* tw = buf0 + nbuf * tileN;                      // twiddles of the y axis
-  uint64_t* full = reinterpret_cast<uint64_t*>(tw + a.twby / sizeof(float2));   // [nbuf]
-  int* fail = reinterpret_cast<int*>(full + nbuf);
-  const int nxt = (a.nx + TX - 1) / TX;
-  const int ntiles = nxt * a.nz * 3;
-  const int B = a.yb, nbox = a.nyr / B;
-  const uint32_t tile_bytes = (uint32_t)(nbox * B * TX * sizeof(float2));
-  if ((int)blockIdx.x >= ntiles) return;
-  if (!block_setup_n(buf0, full, nbuf, fail, a.err)) return;
-  auto issue = [&](int tt, int bb, uint32_t extra) {
-    mbar_arrive_expect_tx(&full[bb], tile_bytes + extra);
-    const int xt = tt % nxt, r = tt / nxt;
-    const int z = r % a.nz, c = r / a.nz;
-    for (int b = 0; b < nbox; ++b) tma_load_4d(buf0 + bb * tileN + b * B * TX, &tm, xt * TX, b * B, z, c, &full[bb]);
-  };
-  const int tid = threadIdx.x, nth = blockDim.x;
-  const int G = gridDim.x;
-  if (tid == 0) {
-    issue(blockIdx.x, 0, a.twby);   // the first tile's barrier also counts the twiddles
-    bulk_load(tw, a.twy, a.twby, &full[0]);
-    for (int d = 1; d < nbuf - 1; ++d)
-      if ((int)blockIdx.x + d * G < ntiles) issue(blockIdx.x + d * G, d, 0);
-  }
-  int b = 0;
-  for (int i = 0, t = blockIdx.x; t < ntiles; ++i, t += G, b = (b + 1 == nbuf) ? 0 : b + 1) {
-    float2* cur = buf0 + b * tileN;
-    if (!block_wait(&full[b], fail, a.err, (uint32_t)((i / nbuf) & 1))) return;
-    auto prefetch = [&] {
-      const int tn = t + (nbuf - 1) * G;
-      if (tid == 0 && tn < ntiles) {
-        bulk_wait_read_all();   // the store of tile i - 1 has left the buffer
-        issue(tn, b == 0 ? nbuf - 1 : b - 1, 0);
-      }
-    };
-    col_stages<INV, TX, 1, MAXR, OCC == 1>(cur, 0, a.ay, 0, a.ay.ns, tw, tid, nth, prefetch);
-    fence_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      const int xt = t % nxt, r = t / nxt;
-      const int z = r % a.nz, c = r / a.nz;
-      for (int bx = 0; bx < nbox; ++bx) tma_store_4d(&tm, xt * TX, bx * B, z, c, cur + bx * B * TX);
-      bulk_commit();
-    }
-  }
-  if (tid == 0) bulk_wait_all();
-}
-
-// Persistent z pass (same pipeline as the y pass, one block per SM): forward stages 0 .. s-2
-// of the three components of a tile, the fused last forward stage + k-space multiply + first
-// inverse stage (single columns, 3 R values in registers; the z wave numbers come from shared
-// memory, the x and y ones from the global tables), inverse stages s-2 .. 0.
-template <int TX>
-__global__ void __launch_bounds__(kYZThreads, 1) k_zpass_green(const __grid_constant__ CUtensorMap tm,
-                                                               const IterArgs a) {
-  constexpr int MAXR = 16;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int nzr = a.nzr;
-  const int cs = nzr * TX, tileN = 3 * cs, nbuf = a.nbuf_z;
-  float2* buf0 = reinterpret_cast<float2*>(smem_raw);   // nbuf x [3][nzr][TX]
-  float2* tw = buf0 + nbuf * tileN;                      // twiddles of the z axis
-  float2* pqz = tw + a.twbz / sizeof(float2);            // wave numbers of the z positions
-  uint64_t* full = reinterpret_cast<uint64_t*>(pqz + a.pqbz / sizeof(float2));   // [nbuf]
-  int* fail = reinterpret_cast<int*>(full + nbuf);
-  const int nxt = (a.nx + TX - 1) / TX;
-  const int ntiles = nxt * a.ny;
-  const int B = a.zb, nbox = nzr / B;
-  const uint32_t tile_bytes = (uint32_t)(3 * nbox * B * TX * sizeof(float2));
-  if ((int)blockIdx.x >= ntiles) return;
-  if (!block_setup_n(buf0, full, nbuf, fail, a.err)) return;
-  auto issue = [&](int tt, int bb, uint32_t extra) {
-    mbar_arrive_expect_tx(&full[bb], tile_bytes + extra);
-    const int xt = tt % nxt, y = tt / nxt;
-    for (int c = 0; c < 3; ++c)
-      for (int b = 0; b < nbox; ++b)
-        tma_load_4d(buf0 + bb * tileN + (c * nzr + b * B) * TX, &tm, xt * TX, y, b * B, c, &full[bb]);
-  };
-  const int tid = threadIdx.x, nth = blockDim.x;
-  const int G = gridDim.x;
-  if (tid == 0) {
-    issue(blockIdx.x, 0, a.twbz + a.pqbz);   // the first tile's barrier also counts the tables
-    bulk_load(tw, a.twz, a.twbz, &full[0]);
-    bulk_load(pqz, a.pqz, a.pqbz, &full[0]);
-    for (int d = 1; d < nbuf - 1; ++d)
-      if ((int)blockIdx.x + d * G < ntiles) issue(blockIdx.x + d * G, d, 0);
-  }
-  const int ns = a.az.ns;
-  const IPStage sl = ip_decode_stage(a.az, ns - 1);
-  int b = 0;
-  for (int i = 0, t = blockIdx.x; t < ntiles; ++i, t += G, b = (b + 1 == nbuf) ? 0 : b + 1) {
-    float2* cur = buf0 + b * tileN;
-    if (!block_wait(&full[b], fail, a.err, (uint32_t)((i / nbuf) & 1))) return;
-    auto prefetch = [&] {
-      const int tn = t + (nbuf - 1) * G;
-      if (tid == 0 && tn < ntiles) {
-        bulk_wait_read_all();
-        issue(tn, b == 0 ? nbuf - 1 : b - 1, 0);
-      }
-    };
-    const int xt = t % nxt, y = t / nxt;
-    const int x0 = xt * TX;
-    const float2 pqy = __ldg(&a.pqy[y]);
-    col_stages<false, TX, 3, MAXR, true>(cur, cs, a.az, 0, ns - 1, tw, tid, nth, prefetch);
-    radix_dispatch<MAXR>(sl.R, [&](auto Ri) {
-      constexpr int R = decltype(Ri)::value;
-      ipz_fused<R, TX>(cur, cs, sl, tid, nth, [&](int col, int pos, float2& X0, float2& X1, float2& X2) {
-        const float2 px = __ldg(&a.pqx[x0 + col]);   // the table is padded past nx
-        const float2 pz = pqz[pos];
-        green(px.x, pqy.x, pz.x, px.y, pqy.y, pz.y, a.kt2, a.invN, X0, X1, X2);
-      });
-    });
-    __syncthreads();
-    if (ns == 1) prefetch();
-    col_stages<true, TX, 3, MAXR, true>(cur, cs, a.az, 0, ns - 1, tw, tid, nth, NoHookIP{});
-    fence_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      for (int c = 0; c < 3; ++c)
-        for (int bb = 0; bb < nbox; ++bb) tma_store_4d(&tm, x0, y, bb * B, c, cur + (c * nzr + bb * B) * TX);
-      bulk_commit();
-    }
-  }
-  if (tid == 0) bulk_wait_all();
-}
 
 template <class F>
 cudaError_t with_tx(int tx, F&& f) {
@@ -229,82 +28,35 @@ cudaError_t with_tx(int tx, F&& f) {
 
 }  // namespace
 
-// nbuf tiles + twiddles (+ z wave numbers) + mbarriers (8 bytes each) + 8 bytes for the
-// failure flag
-size_t ypass_smem(const IterArgs& a) {
-  return (size_t)a.nbuf_y * a.nyr * a.tx_y * sizeof(float2) + a.twby + 8 * a.nbuf_y + 8;
-}
-size_t zpass_smem(const IterArgs& a) {
-  return (size_t)3 * a.nbuf_z * a.nzr * a.tx_z * sizeof(float2) + a.twbz + a.pqbz + 8 * a.nbuf_z + 8;
-}
 int ypass_tiles(const IterArgs& a) { return (a.nx + a.tx_y - 1) / a.tx_y * a.nz * 3; }
 int zpass_tiles(const IterArgs& a) { return (a.nx + a.tx_z - 1) / a.tx_z * a.ny; }
 
-template <class F>
-cudaError_t with_occ(int occ, F&& f) {
-  return occ == 2 ? f(std::integral_constant<int, 2>{}) : f(std::integral_constant<int, 1>{});
-}
-
 // Persistent grids: as many blocks as fit on the device at once (capped by the tile count).
 cudaError_t yz_grid_sizes(IterArgs& a, int sms) {
-  cudaError_t e = with_tx(a.tx_y, [&](auto T) {
-    return with_occ(a.occ_y, [&](auto O) {
-      constexpr int TX = decltype(T)::value, OCC = decltype(O)::value;
-      int occ = 0;
-      cudaError_t e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ypass<TX, false, OCC>, kYZThreads,
-                                                                     ypass_smem(a));
-      if (e1 == cudaSuccess) a.grid_y = std::max(1, std::min(ypass_tiles(a), sms * std::max(1, occ)));
-      return e1;
-    });
-  });
+  int occ = 0;
+  cudaError_t e = with_tx(a.tx_y, [&](auto T) { return y_occupancy<decltype(T)::value>(a, &occ); });
   if (e != cudaSuccess) return e;
-  return with_tx(a.tx_z, [&](auto T) {
-    constexpr int TX = decltype(T)::value;
-    int occ = 0;
-    cudaError_t e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_zpass_green<TX>, kYZThreads,
-                                                                   zpass_smem(a));
-    if (e1 == cudaSuccess) a.grid_z = std::max(1, std::min(zpass_tiles(a), sms * std::max(1, occ)));
-    return e1;
-  });
+  a.grid_y = std::max(1, std::min(ypass_tiles(a), sms * std::max(1, occ)));
+  e = with_tx(a.tx_z, [&](auto T) { return z_occupancy<decltype(T)::value>(a, &occ); });
+  if (e != cudaSuccess) return e;
+  a.grid_z = std::max(1, std::min(zpass_tiles(a), sms * std::max(1, occ)));
+  return cudaSuccess;
 }
 
 cudaError_t launch_ypass(const CUtensorMap& tm, const IterArgs& a, bool inverse, cudaStream_t s) {
-  return with_tx(a.tx_y, [&](auto T) {
-    return with_occ(a.occ_y, [&](auto O) {
-      constexpr int TX = decltype(T)::value, OCC = decltype(O)::value;
-      if (inverse)
-        k_ypass<TX, true, OCC><<<a.grid_y, kYZThreads, ypass_smem(a), s>>>(tm, a);
-      else
-        k_ypass<TX, false, OCC><<<a.grid_y, kYZThreads, ypass_smem(a), s>>>(tm, a);
-      return cudaGetLastError();
-    });
-  });
+  return with_tx(a.tx_y, [&](auto T) { return y_launch<decltype(T)::value>(tm, a, inverse, s); });
 }
 
 cudaError_t launch_zpass_green(const CUtensorMap& tm, const IterArgs& a, cudaStream_t s) {
-  return with_tx(a.tx_z, [&](auto T) {
-    constexpr int TX = decltype(T)::value;
-    k_zpass_green<TX><<<a.grid_z, kYZThreads, zpass_smem(a), s>>>(tm, a);
-    return cudaGetLastError();
-  });
+  return with_tx(a.tx_z, [&](auto T) { return z_launch<decltype(T)::value>(tm, a, s); });
 }
 
 cudaError_t yzpass_set_smem_limit(int bytes) {
   cudaError_t e = cudaSuccess;
-  auto set = [&](const void* f) {
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  };
-  auto set_tx = [&](auto T) {
-    constexpr int TX = decltype(T)::value;
-    set((const void*)k_ypass<TX, false, 1>);
-    set((const void*)k_ypass<TX, true, 1>);
-    set((const void*)k_ypass<TX, false, 2>);
-    set((const void*)k_ypass<TX, true, 2>);
-    set((const void*)k_zpass_green<TX>);
-  };
-  set_tx(std::integral_constant<int, 4>{});
-  set_tx(std::integral_constant<int, 8>{});
-  set_tx(std::integral_constant<int, 16>{});
+  for (int tx : {4, 8, 16}) {
+    if (e == cudaSuccess) e = with_tx(tx, [&](auto T) { return y_set_smem<decltype(T)::value>(bytes); });
+    if (e == cudaSuccess) e = with_tx(tx, [&](auto T) { return z_set_smem<decltype(T)::value>(bytes); });
+  }
   return e;
 }
 

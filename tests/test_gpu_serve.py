@@ -144,9 +144,9 @@ def test_a_large_request_is_not_starved_by_a_stream_of_small_ones():
     small = GridSpec(32, 32, 32, lam / 8, lam, 1.0, (4, 4, 4), (4, 4, 4))
     large = GridSpec(64, 64, 64, lam / 8, lam, 1.0, (8, 8, 8), (8, 8, 8))
 
-    def slot_bytes(g):   # the server's footprint of a slot: plan, eps, E, E_adj, gradient
-        nxp = (g.nx + 15) // 16 * 16
-        return nxp * g.ny * g.nz * 56 + g.nx * g.ny * g.nz * 56 + (16 << 20)
+    def slot_bytes(g):   # the server's footprint of a slot: plan (planes of up to ny + 1
+        nxp = (g.nx + 15) // 16 * 16   # padded rows), eps, E, E_adj, gradient
+        return nxp * (g.ny + 1) * g.nz * 56 + g.nx * g.ny * g.nz * 56 + (16 << 20)
 
     budget = (slot_bytes(large) + (1 << 20)) / 1e9
     eps_s = inputs.random_eps(32, 32, 32, seed=21)
