@@ -70,10 +70,10 @@ __global__ void k_k2_maxdev(const float* __restrict__ eps, int nx, int ny, int n
     voxel_xyz(i, nx, ny, x, y, z);
     const double re = kv2 * (double)eps[i] - k0sq;
     const double im = kv2 * layer_combine(sx[x], sy[y], sz[z], corner_max);
-    m = fmax(m, sqrt(re * re + im * im));
+    m = fmax(m, re * re + im * im);   // squared: one square root per block, not per voxel
   }
   m = block_reduce(m, [](double p, double q) { return fmax(p, q); }, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = m;
+  if (threadIdx.x == 0) part[blockIdx.x] = sqrt(m);   // sqrt is monotonic: the same maximum
 }
 
 // V in the y-blocked layout of the iteration (row padding stays zero).

@@ -67,7 +67,12 @@ class CBSPlan:
 
     def __init__(self, nx: int, ny: int, nz: int, pitch: float, lam: float, n_bg: float = 1.0,
                  pad_lo=(0, 0, 0), pad_hi=None, tol: float = 1e-6, max_iter: int = 100000,
-                 check_every: int = 32, device=None, stream: Optional[torch.cuda.Stream] = None):
+                 check_every: int = 32, device=None, stream: Optional[torch.cuda.Stream] = None,
+                 layer_round_trip: float = 0.0, layer_power: float = 0.0, layer_corner_max: bool = False):
+        """Absorbing layers: layer_round_trip (the amplitude a normally incident plane wave keeps
+        after crossing a layer and back; 0 selects 1e-4), layer_power (ramp exponent; 0 selects
+        2) and layer_corner_max (where layers overlap the largest applies instead of the sum);
+        see cbs_plan_desc in include/cbs.h."""
         self.lib = L.lib()
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         if pad_hi is None:
@@ -80,7 +85,8 @@ class CBSPlan:
             s = stream if stream is not None else torch.cuda.current_stream(self.device)
             d = L.cbs_plan_desc(nx, ny, nz, pitch, lam, n_bg, (ctypes.c_int * 3)(*pad_lo),
                                 (ctypes.c_int * 3)(*pad_hi), tol, max_iter, check_every,
-                                ctypes.c_void_p(s.cuda_stream))
+                                ctypes.c_void_p(s.cuda_stream), float(layer_round_trip), float(layer_power),
+                                1 if layer_corner_max else 0)
             h = ctypes.c_void_p()
             L.check(self.lib.cbs_plan(ctypes.byref(h), ctypes.byref(d)))
         self.handle = h

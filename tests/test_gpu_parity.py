@@ -90,6 +90,29 @@ def test_fixed_iterations_plane_wave(case):
     assert abs(st.rel_resid - ref.history[-1] / ref.history[0]) <= 1e-4 * (ref.history[-1] / ref.history[0])
 
 
+@pytest.mark.parametrize("rt,power,corner", [(1e-2, 2.0, "max"), (1e-3, 3.0, "sum")])
+def test_absorbing_layer_options_match_the_oracle(rt, power, corner):
+    """The layer options (round trip, ramp exponent, corner rule) give the oracle's potential
+    (same splitting) and field at equal iterations, on a grid with different pads per face."""
+    torch = _torch()
+    nx, ny, nz = 40, 36, 44
+    lo, hi = (4, 5, 6), (6, 4, 5)
+    g = co.Grid(nx, ny, nz, LAM / 8, LAM, 1.0, lo, hi, round_trip=rt, power=power, corner=corner)
+    eps = inputs.random_eps(nx, ny, nz, seed=12)
+    K = 24
+    ref = co.forward(g, eps, co.plane_wave_source(g), tol=0.0, max_iter=K)
+    from paper_2506_15411_gb300 import CBSPlan, PlaneWave
+    with CBSPlan(nx, ny, nz, g.pitch, LAM, 1.0, lo, hi, tol=0.0, max_iter=K, check_every=8, layer_round_trip=rt,
+                 layer_power=power, layer_corner_max=(corner == "max")) as plan:
+        plan.set_permittivity(to_dev(eps))
+        k0sq, epsilon = plan.splitting()
+        E, st = plan.forward(PlaneWave())
+        torch.cuda.synchronize()
+    assert abs(k0sq - ref.split.k0sq) <= 1e-6 * abs(ref.split.k0sq)
+    assert abs(epsilon - ref.split.epsilon) <= 1e-6 * ref.split.epsilon
+    assert rel_l2(E.cpu().numpy(), ref.E) <= 2e-5
+
+
 def test_warm_start_user_source_one_and_three_iterations():
     torch = _torch()
     g = co.Grid(40, 33, 28, LAM / 8, LAM, 1.0, (4, 3, 4), (4, 3, 4))

@@ -19,9 +19,9 @@ pytestmark = pytest.mark.gpu
 LAM = 1.064e-6
 
 
-def _desc(L, nx, ny, nz, pitch, lo, hi, stream=0, n_bg=1.0):
+def _desc(L, nx, ny, nz, pitch, lo, hi, stream=0, n_bg=1.0, rt=0.0, power=0.0, corner=0):
     return L.cbs_plan_desc(nx, ny, nz, pitch, LAM, n_bg, (ctypes.c_int * 3)(*lo), (ctypes.c_int * 3)(*hi),
-                           0.0, 1, 1, ctypes.c_void_p(stream))
+                           0.0, 1, 1, ctypes.c_void_p(stream), rt, power, corner)
 
 
 def _noalloc(L, lib, desc, eps):
@@ -38,17 +38,21 @@ def test_noalloc_splitting_matches_plan_on_two_calls_in_a_row():
     from paper_2506_15411_gb300 import _lib as L
     lib = L.lib()
     # a large grid first (many block partials), then a small one that reuses fewer of them
-    # (a third grid with a background index other than 1 checks the layer strength's n_bg)
-    cases = [((96, 80, 110), LAM / 8, (8, 6, 10), (7, 8, 9), 1.0, 2.4, 31, 1.0),
-             ((20, 18, 22), LAM / 6, (3, 2, 4), (2, 3, 1), 1.3, 1.6, 32, 1.0),
-             ((40, 36, 30), LAM / 8, (4, 5, 6), (6, 5, 4), 1.7, 2.2, 34, 1.33)]
-    for (nx, ny, nz), pitch, lo, hi, emin, emax, seed, n_bg in cases:
+    # (a third grid with a background index other than 1 checks the layer strength's n_bg, a
+    # fourth the layer options)
+    cases = [((96, 80, 110), LAM / 8, (8, 6, 10), (7, 8, 9), 1.0, 2.4, 31, 1.0, (0.0, 0.0, 0)),
+             ((20, 18, 22), LAM / 6, (3, 2, 4), (2, 3, 1), 1.3, 1.6, 32, 1.0, (0.0, 0.0, 0)),
+             ((40, 36, 30), LAM / 8, (4, 5, 6), (6, 5, 4), 1.7, 2.2, 34, 1.33, (0.0, 0.0, 0)),
+             ((40, 36, 30), LAM / 8, (4, 5, 6), (6, 5, 4), 1.0, 2.2, 35, 1.0, (1e-2, 3.0, 1))]
+    for (nx, ny, nz), pitch, lo, hi, emin, emax, seed, n_bg, (rt, pw, cm) in cases:
         eps = torch.from_numpy(inputs.random_eps(nx, ny, nz, lo=emin, hi=emax, seed=seed)).cuda()
-        with CBSPlan(nx, ny, nz, pitch, LAM, n_bg, lo, hi) as plan:
+        with CBSPlan(nx, ny, nz, pitch, LAM, n_bg, lo, hi, layer_round_trip=rt, layer_power=pw,
+                     layer_corner_max=bool(cm)) as plan:
             plan.set_permittivity(eps)
             k0_ref, ep_ref = plan.splitting()
         torch.cuda.synchronize()
-        rc, k0, ep = _noalloc(L, lib, _desc(L, nx, ny, nz, pitch, lo, hi, n_bg=n_bg), eps)
+        rc, k0, ep = _noalloc(L, lib, _desc(L, nx, ny, nz, pitch, lo, hi, n_bg=n_bg, rt=rt, power=pw, corner=cm),
+                              eps)
         assert rc == L.CBS_OK, lib.cbs_last_error()
         assert abs(k0 - k0_ref) <= 1e-12 * abs(k0_ref)
         assert abs(ep - ep_ref) <= 1e-12 * ep_ref
