@@ -19,7 +19,9 @@ After the timed region:
     the same with gentler absorbing layers ("..._gentle_layers": round trip 1e-2, the largest
     overlapping profile in edges and corners), which lower the shift epsilon and the iterations;
   * "cufft_comparison": the same iteration written with cuFFT and element-wise torch kernels;
-  * "serving": a short seeded request stream through the continuous-batching server.
+  * "serving": a seeded request stream over the five serving grid sizes (64^3 .. 384x384x256,
+    spheres and lenses, forward and forward + adjoint, gentler layers by default) through the
+    continuous-batching server, with the same requests' single-solve times beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
@@ -492,11 +494,12 @@ def run_gpu(args, rank, world, local_rank):
     c2g = secondary_c2(args, stream, dev, GENTLE_LAYERS) if args.c2 and args.tol > 0 else None
     serving = None
     if args.serve_requests > 0 and args.tol > 0:
-        # served-solve latency (the metric's third part): a seeded stream of small grids
-        # through the continuous-batching server
+        # served-solve latency (the metric's third part): a seeded stream over the five grid
+        # sizes of the serving workload through the continuous-batching server, each request
+        # also solved alone for the single-solve percentiles
         from paper_2506_15411_gb300.serve import measure_stream
         serving = measure_stream(args.serve_requests, [inputs.parse_size(v) for v in args.serve_sizes],
-                                 tol=args.tol)
+                                 tol=args.tol, layers=args.serve_layers)
     traffic = load_traffic(dom)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -553,10 +556,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-c2", dest="c2", action="store_false",
                     help="skip the converged 275x275x315 lens design iteration")
-    ap.add_argument("--serve-requests", type=int, default=12,
+    ap.add_argument("--serve-requests", type=int, default=20,
                     help="requests of the served-latency stream after the timed region (0: none; "
                          "skipped when --tol <= 0)")
-    ap.add_argument("--serve-sizes", nargs="+", default=["64", "128"], help="grid sizes of that stream")
+    ap.add_argument("--serve-sizes", nargs="+", default=["64", "128", "192x192x128", "256x256x192", "384x384x256"],
+                    help="grid sizes of that stream")
+    ap.add_argument("--serve-layers", choices=["default", "gentle"], default="gentle",
+                    help="absorbing layers of the stream's requests")
     ap.add_argument("--cufft-iters", type=int, default=20,
                     help="iterations of the cuFFT comparison timed after the timed region (0: none)")
     ap.add_argument("--print-digest", action="store_true", help="print the CUDA source digest and exit")

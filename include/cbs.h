@@ -286,20 +286,26 @@ int cbs_design_step(cbs_design_t design, float* h_dev, const cbs_source* src, co
 
 /* ---------------------------------------------------------------- serving
  * A request server with continuous batching.  Submitted requests queue; a worker thread
- * admits them into slots (a plan, its stream and field buffers for one grid shape) while
- * the device-memory budget and max_active allow, and advances every admitted request one
- * block of check_every iterations at a time without waiting on any one of them, so that
- * requests arriving while others run start as soon as a slot and memory are free and their
- * work interleaves on the GPU.  Idle slots are kept for later requests of the same shape and
- * evicted, least recently used first, when memory is needed.  Fields stay in the slot's
- * device memory; only the outputs a request asks for are copied out.  A request's result
- * does not depend on what else runs: slots share no device memory and every kernel and
- * reduction has a fixed order.  The server works on the device current at creation.  Not a
- * part of the paper; the serving layer of this library. */
+ * admits them while the device-memory budget and max_active allow.  Requests of one grid
+ * shape share a batch: a plan whose arrays hold up to min(8, max_active) requests side by
+ * side (seats), each with its own permittivity, splitting and source.  The worker advances
+ * every batch one block of check_every iterations at a time without waiting on any one of
+ * them; each launch of a block carries every iterating request of the batch (the kernels'
+ * tile space has a request index), so same-shape requests in flight share the launches, and
+ * batches of different shapes run side by side on their own streams.  A request arriving
+ * while others run takes a free seat at the next block, or a new batch when memory allows;
+ * a batch is created with as many seats as the budget leaves room for.  Batches without
+ * requests are kept for later requests of their shape and evicted, least recently used
+ * first, when memory is needed.  Fields stay in the seat's device memory; only the outputs a
+ * request asks for are copied out.  A request's result does not depend on what else runs:
+ * its blocks in a launch are those of its own persistent grid, so its tiles and the order of
+ * its residual sums are fixed, seats share no device memory, and the stopping decision uses
+ * its own residuals only.  The server works on the device current at creation.  Not a part
+ * of the paper; the serving layer of this library. */
 typedef struct cbs_server_s* cbs_server_t;
 
 typedef struct {
-  double hbm_budget_bytes;  /* device bytes the slots may hold; 0 = 80 % of the free memory */
+  double hbm_budget_bytes;  /* device bytes the batches may hold; 0 = 80 % of the free memory */
   int max_active;           /* requests admitted at once (>= 1) */
   double tol;               /* solver settings of every request (as in cbs_plan_desc) */
   int max_iter;
@@ -349,8 +355,14 @@ int cbs_server_submit(cbs_server_t server, const cbs_request* req, long long* id
  * for the first; *n receives the count (0 on timeout). */
 int cbs_server_take(cbs_server_t server, cbs_result* out, int max, double timeout_s, int* n);
 
-/* Requests waiting for admission, requests admitted, device bytes held by slots. */
+/* Requests waiting for admission, requests admitted, device bytes held by batches. */
 int cbs_server_info(cbs_server_t server, long long* queued, long long* active, double* bytes_used);
+
+/* Launch sharing so far: *launches = iterations launched (each the four passes of one
+ * iteration of one batch), *request_iterations = the request iterations they carried (their
+ * sum of members), *max_members = the most requests one launch carried.  Any pointer may be
+ * NULL. */
+int cbs_server_sharing(cbs_server_t server, long long* launches, long long* request_iterations, int* max_members);
 
 /* Self-test of the failure path of the tile kernels: every wait of theirs on a tensor copy is
  * bounded and, when it gives up, records an error the host reads after the block of

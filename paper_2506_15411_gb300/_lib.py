@@ -36,6 +36,7 @@ EXPORTS = ("cbs_plan", "cbs_set_permittivity", "cbs_get_splitting", "cbs_set_sol
            "cbs_design_get_state", "cbs_design_set_state",
            "cbs_design_permittivity", "cbs_design_height_gradient", "cbs_design_adam", "cbs_design_step",
            "cbs_server_create", "cbs_server_destroy", "cbs_server_submit", "cbs_server_take", "cbs_server_info",
+           "cbs_server_sharing",
            "cbs_selftest_wait_timeout")
 
 # cbs_pass_times slots: the series' first forward x pass (launched once per series, not
@@ -122,6 +123,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "cbs_server_submit": (c_int, [P, POINTER(cbs_request), POINTER(ctypes.c_longlong)]),
         "cbs_server_take": (c_int, [P, POINTER(cbs_result), c_int, c_double, POINTER(c_int)]),
         "cbs_server_info": (c_int, [P, POINTER(ctypes.c_longlong), POINTER(ctypes.c_longlong), POINTER(c_double)]),
+        "cbs_server_sharing": (c_int, [P, POINTER(ctypes.c_longlong), POINTER(ctypes.c_longlong), POINTER(c_int)]),
         "cbs_design_create": (c_int, [POINTER(c_void_p), P, POINTER(cbs_design_desc)]),
         "cbs_design_destroy": (None, [P]),
         "cbs_design_reset": (c_int, [P]),

@@ -105,13 +105,15 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// 5D map of the workspace W in its y-blocked layout, viewed as [3][nyb][nz][yblk][nx]
+// 5D map of the workspace W in its y-blocked layout, viewed as [3 seats][nyb][nz][yblk][nx]
 // complex64 (8-byte elements) with row pitch nxp; box = {bx, by, bz, 1, 1} over (x, y in
 // block, z).  Elements beyond nx or nz read as zero and are not written.
-bool encode_w_map(CUtensorMap* tm, float2* W, int nx, int ny, int nz, int nxp, int yblk, int bx, int by, int bz) {
+bool encode_w_map(CUtensorMap* tm, float2* W, int nx, int ny, int nz, int nxp, int yblk, int seats, int bx, int by,
+                  int bz) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
-  const cuuint64_t dims[5] = {(cuuint64_t)nx, (cuuint64_t)yblk, (cuuint64_t)nz, (cuuint64_t)(ny / yblk), 3};
+  const cuuint64_t dims[5] = {(cuuint64_t)nx, (cuuint64_t)yblk, (cuuint64_t)nz, (cuuint64_t)(ny / yblk),
+                              (cuuint64_t)3 * seats};
   const cuuint64_t row = (cuuint64_t)nxp * sizeof(float2);
   const cuuint64_t strides[4] = {row, row * yblk, row * yblk * nz, row * ny * nz};
   const cuuint32_t box[5] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1, 1};
@@ -217,7 +219,7 @@ int graph_block(cbs_plan_s* p, const IterArgs& a, int n, bool& used) {
   used = false;
   cudaGraphExec_t exec = nullptr;
   for (auto& g : p->graphs)
-    if (g.E == a.E && g.iters == n && same_source(g.src, a.src)) exec = g.exec;
+    if (g.E == a.E && g.iters == n && same_source(g.src, a.mem[0].src)) exec = g.exec;
   if (!exec) {
     if (p->graphs.size() >= 8) drop_graphs(p);
     cudaGraph_t g = nullptr;
@@ -235,7 +237,7 @@ int graph_block(cbs_plan_s* p, const IterArgs& a, int n, bool& used) {
     e = cudaGraphInstantiate(&ex, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(CBS_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
-    p->graphs.push_back(GraphEntry{a.E, a.src, n, ex});
+    p->graphs.push_back(GraphEntry{a.E, a.mem[0].src, n, ex});
     exec = ex;
   }
   CK(cudaGraphLaunch(exec, p->stream));
@@ -277,12 +279,13 @@ int make_source(cbs_plan_s* p, const cbs_source* src, SourceArgs& s) {
 }
 
 
-// Copy a field between the caller's dense layout [3][nz][ny][nx] and the plan's y-blocked
-// one (the row padding is never written here: it stays zero).
-cudaError_t field_copy(const cbs_plan_s* p, float2* dense, bool to_dense) {
+// Copy a field between the caller's dense layout [3][nz][ny][nx] and the y-blocked iterate of
+// seat `seat` (the row padding is never written here: it stays zero).
+cudaError_t field_copy(const cbs_plan_s* p, int seat, float2* dense, bool to_dense, cudaStream_t s) {
   const IterArgs& a = p->base;
-  return to_dense ? launch_field_layout(p->Ei, dense, true, a.nx, a.ny, a.nz, a.nxp, a.yblk, p->stream)
-                  : launch_field_layout(dense, p->Ei, false, a.nx, a.ny, a.nz, a.nxp, a.yblk, p->stream);
+  float2* Ei = p->Ei + (size_t)seat * 3 * a.Nw;
+  return to_dense ? launch_field_layout(Ei, dense, true, a.nx, a.ny, a.nz, a.nxp, a.yblk, s)
+                  : launch_field_layout(dense, Ei, false, a.nx, a.ny, a.nz, a.nxp, a.yblk, s);
 }
 
 // Enqueue the next block of iterations, the copy of its residual sums and of the error flag,
@@ -304,21 +307,11 @@ int series_enqueue_block(cbs_plan_s* p, SeriesRun& R) {
   return CBS_OK;
 }
 
-// Host side of a completed block: error flag, pass times, residuals, stopping rules.
-// Sets R.rc on an error and returns whether iterating is over.
-bool series_absorb_block(cbs_plan_s* p, SeriesRun& R) {
-  R.iterating = false;
-  nvtxRangeEnd(R.blk_range);
-  R.blk_range = 0;
-  if (*p->err_host) {
-    R.rc = fail(CBS_ERR_CUDA, "a tensor-copy wait timed out in an FFT pass (device error %d)", *p->err_host);
-    return true;
-  }
-  R.rc = collect_pass_times(p);
-  if (R.rc) return true;
+// The stopping rules on a block's residual sums (one run; shared with the request server).
+bool series_absorb_residuals(const cbs_plan_s* p, SeriesRun& R, const double* h) {
   for (int k = 0; k < R.m; ++k) {
     ++R.it;
-    const double r = std::sqrt(p->hist_host[k]);
+    const double r = std::sqrt(h[k]);
     if (R.r0 < 0) R.r0 = r;
     R.rel = R.r0 > 0 ? r / R.r0 : 0.0;
     if (!std::isfinite(r) || R.rel > 1e4) {
@@ -350,10 +343,25 @@ bool series_absorb_block(cbs_plan_s* p, SeriesRun& R) {
   return done || R.it >= p->d.max_iter;
 }
 
+// Host side of a completed block: error flag, pass times, residuals, stopping rules.
+// Sets R.rc on an error and returns whether iterating is over.
+bool series_absorb_block(cbs_plan_s* p, SeriesRun& R) {
+  R.iterating = false;
+  nvtxRangeEnd(R.blk_range);
+  R.blk_range = 0;
+  if (*p->err_host) {
+    R.rc = fail(CBS_ERR_CUDA, "a tensor-copy wait timed out in an FFT pass (device error %d)", *p->err_host);
+    return true;
+  }
+  R.rc = collect_pass_times(p);
+  if (R.rc) return true;
+  return series_absorb_residuals(p, R, p->hist_host);
+}
+
 // Copy the iterate back into the caller's field (also after an error: E then holds the last
 // iterate), with blk_ev marking its end.
 void series_enqueue_copy_out(cbs_plan_s* p, SeriesRun& R) {
-  cudaError_t e = field_copy(p, R.E, true);
+  cudaError_t e = field_copy(p, 0, R.E, true, p->stream);
   if (e == cudaSuccess) e = cudaEventRecord(p->blk_ev, p->stream);
   if (e != cudaSuccess) {
     if (R.rc == CBS_OK) R.rc = fail(CBS_ERR_CUDA, "field copy-out: %s", cudaGetErrorString(e));
@@ -379,7 +387,8 @@ void series_begin(cbs_plan_s* p, float2* E, const SourceArgs& src, int warm, Ser
   }
   R.a = p->base;
   R.a.E = p->Ei;   // iterate on the plan's padded copy; the caller's E is read and written once
-  R.a.src = src;
+  R.a.nmem = 1;    // the plan's own solves use seat 0
+  R.a.mem[0].src = src;
   // every run starts from a clean error flag and residual counter: a run that a timed-out
   // tensor-copy wait ended left both behind, and everything else it touched (W, the
   // iterate, the partial sums) is recomputed from the plan's inputs below
@@ -415,7 +424,7 @@ void series_begin(cbs_plan_s* p, float2* E, const SourceArgs& src, int warm, Ser
     e = cudaMemsetAsync(p->Ei, 0, 3 * R.a.Nw * sizeof(float2), p->stream);
   }
   if (warm && e == cudaSuccess)
-    e = field_copy(p, E, false);
+    e = field_copy(p, 0, E, false, p->stream);
   if (e == cudaSuccess) e = launch_xpass_fwd(R.a, p->stream);   // W of the first iteration
   if (e != cudaSuccess) {
     R.rc = fail(CBS_ERR_CUDA, "field copy-in: %s", cudaGetErrorString(e));
@@ -514,10 +523,53 @@ extern "C" {
 
 const char* cbs_last_error(void) { return g_err.c_str(); }
 
-int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
-  g_err.clear();
+}  // extern "C"
+
+namespace cbs {
+
+// Splitting and potential of seat `seat` from a permittivity on the device (synchronous on
+// stream s; uses the plan's set-up scratch): k0^2 the mid-range of k^2, epsilon the largest
+// |k^2 - k0^2| over the grid (absorbing layers included), V = k^2 - k0^2 - i epsilon in the
+// seat's slice.  The scaled k0^2 and epsilon land in seat_k0sq / seat_eps.
+int seat_permittivity(cbs_plan_s* p, int seat, const float* eps, cudaStream_t s) {
+  const int B = p->red_blocks;
+  CK(launch_eps_minmax(eps, p->N, p->pmin, p->pmax, p->pbad, B, s));
+  std::vector<float> mn(B), mx(B);
+  std::vector<int> bad(B);
+  CK(cudaMemcpyAsync(mn.data(), p->pmin, B * sizeof(float), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(mx.data(), p->pmax, B * sizeof(float), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(bad.data(), p->pbad, B * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  double lo = 1e300, hi = -1e300;
+  for (int b = 0; b < B; ++b) {
+    if (bad[b]) return fail(CBS_ERR_ARG, "permittivity contains a non-finite value");
+    lo = std::min(lo, (double)mn[b]);
+    hi = std::max(hi, (double)mx[b]);
+  }
+  const double kv2 = (p->kvac * p->pitch) * (p->kvac * p->pitch);
+  const double k0sq = 0.5 * kv2 * (lo + hi);
+  CK(launch_k2_maxdev(eps, p->d.nx, p->d.ny, p->d.nz, p->sx, p->sy, p->sz, p->layers.corner_max, kv2, k0sq,
+                      p->pdev, B, s));
+  std::vector<double> dv(B);
+  CK(cudaMemcpyAsync(dv.data(), p->pdev, B * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  double epsilon = 0.0;
+  for (int b = 0; b < B; ++b) epsilon = std::max(epsilon, dv[b]);
+  if (!(epsilon > 0.0) || !std::isfinite(epsilon))
+    return fail(CBS_ERR_ARG, "epsilon = %g: a lossless homogeneous grid has no convergent splitting", epsilon);
+  CK(launch_build_v(eps, p->d.nx, p->d.ny, p->d.nz, p->base.nxp, p->base.yblk, p->sx, p->sy, p->sz,
+                    p->layers.corner_max, kv2, k0sq, epsilon, p->V + (size_t)seat * p->base.Nw, s));
+  CK(cudaStreamSynchronize(s));
+  p->seat_k0sq[seat] = k0sq;
+  p->seat_eps[seat] = epsilon;
+  return CBS_OK;
+}
+
+// A plan whose arrays hold `seats` requests of the grid side by side (cbs_plan: one).
+int plan_create(cbs_plan_s** out, const cbs_plan_desc* desc, int seats) {
   if (!out || !desc) return fail(CBS_ERR_ARG, "NULL argument");
   *out = nullptr;
+  if (seats < 1 || seats > kMaxMembers) return fail(CBS_ERR_ARG, "seats %d outside [1, %d]", seats, kMaxMembers);
   const cbs_plan_desc& d = *desc;
   const int dims[3] = {d.nx, d.ny, d.nz};
   for (int a = 0; a < 3; ++a) {
@@ -540,6 +592,7 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
 
   cbs_plan_s* p = new cbs_plan_s();
   p->d = d;
+  p->seats = seats;
   p->N = (size_t)d.nx * d.ny * d.nz;
   p->pitch = d.pitch_m;
   p->kvac = 2.0 * kPiD / d.lambda_m;
@@ -671,26 +724,29 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
   a.pqbz = pqbz;
 
   const size_t N = p->N;
-  CKP(cudaMalloc(&p->V, a.Nw * sizeof(float2)));
-  CKP(cudaMemset(p->V, 0, a.Nw * sizeof(float2)));        // row padding stays zero
-  CKP(cudaMalloc(&p->Ei, 3 * a.Nw * sizeof(float2)));
-  CKP(cudaMalloc(&p->W, 3 * a.Nw * sizeof(float2)));
-  CKP(cudaMemset(p->W, 0, 3 * a.Nw * sizeof(float2)));   // row padding stays zero
+  const size_t S = (size_t)seats;
+  CKP(cudaMalloc(&p->V, S * a.Nw * sizeof(float2)));
+  CKP(cudaMemset(p->V, 0, S * a.Nw * sizeof(float2)));        // row padding stays zero
+  CKP(cudaMalloc(&p->Ei, S * 3 * a.Nw * sizeof(float2)));
+  CKP(cudaMalloc(&p->W, S * 3 * a.Nw * sizeof(float2)));
+  CKP(cudaMemset(p->W, 0, S * 3 * a.Nw * sizeof(float2)));   // row padding stays zero
   CKP(cudaMalloc(&p->err_dev, sizeof(int)));
   CKP(cudaMemset(p->err_dev, 0, sizeof(int)));
   CKP(cudaMallocHost(&p->err_host, sizeof(int)));
-  if (!encode_w_map(&p->tmy, p->W, d.nx, d.ny, d.nz, a.nxp, a.yblk, a.tx_y, a.yblk, 1) ||
-      !encode_w_map(&p->tmz, p->W, d.nx, d.ny, d.nz, a.nxp, a.yblk, a.tx_z, 1, a.zb)) {
+  if (!encode_w_map(&p->tmy, p->W, d.nx, d.ny, d.nz, a.nxp, a.yblk, seats, a.tx_y, a.yblk, 1) ||
+      !encode_w_map(&p->tmz, p->W, d.nx, d.ny, d.nz, a.nxp, a.yblk, seats, a.tx_z, 1, a.zb)) {
     fail(CBS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the workspace");
     return bail(CBS_ERR_CUDA);
   }
-  CKP(cudaMalloc(&p->partials, (size_t)xpass_tiles(a) * sizeof(double)));   // >= the x grid
-  CKP(cudaMalloc(&p->counter, sizeof(unsigned)));
-  CKP(cudaMemset(p->counter, 0, sizeof(unsigned)));
-  CKP(cudaMalloc(&p->hist, (size_t)d.check_every * sizeof(double)));
-  CKP(cudaMallocHost(&p->hist_host, (size_t)d.check_every * sizeof(double)));
-  CKP(cudaMalloc(&p->adj_amp, 3 * sizeof(float2)));
-  CKP(cudaMalloc(&p->dobj, sizeof(double)));
+  CKP(cudaMalloc(&p->partials, S * xpass_tiles(a) * sizeof(double)));   // >= seats x the x grid
+  CKP(cudaMalloc(&p->counter, S * sizeof(unsigned)));
+  CKP(cudaMemset(p->counter, 0, S * sizeof(unsigned)));
+  CKP(cudaMalloc(&p->hist, S * d.check_every * sizeof(double)));
+  CKP(cudaMallocHost(&p->hist_host, S * d.check_every * sizeof(double)));
+  CKP(cudaMalloc(&p->adj_amp, S * 3 * sizeof(float2)));
+  CKP(cudaMalloc(&p->dobj, S * sizeof(double)));
+  p->seat_k0sq.assign(seats, 0.0);
+  p->seat_eps.assign(seats, 0.0);
   CKP(cudaMalloc(&p->sx, d.nx * sizeof(double)));
   CKP(cudaMalloc(&p->sy, d.ny * sizeof(double)));
   CKP(cudaMalloc(&p->sz, d.nz * sizeof(double)));
@@ -779,14 +835,28 @@ int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
 
   a.W = p->W;
   a.V = p->V;
+  a.E = p->Ei;
+  a.seats = seats;
+  a.nmem = 1;
+  a.mem[0] = Member{};
   a.err = p->err_dev;
   a.partials = p->partials;
   a.counter = p->counter;
   a.hist = p->hist;
+  a.hist_cap = d.check_every;
   a.invN = (float)(1.0 / (double)N);
 #undef CKP
   *out = p;
   return CBS_OK;
+}
+
+}  // namespace cbs
+
+extern "C" {
+
+int cbs_plan(cbs_plan_t* out, const cbs_plan_desc* desc) {
+  g_err.clear();
+  return plan_create(out, desc, 1);
 }
 
 void cbs_destroy(cbs_plan_t p) {
@@ -847,8 +917,9 @@ int cbs_set_solver(cbs_plan_t p, double tol, int max_iter, int check_every) {
     drop_graphs(p);
     double* h = nullptr;
     double* hh = nullptr;
-    CK(cudaMalloc(&h, (size_t)check_every * sizeof(double)));
-    cudaError_t e = cudaMallocHost(&hh, (size_t)check_every * sizeof(double));
+    const size_t n = (size_t)p->seats * check_every;
+    CK(cudaMalloc(&h, n * sizeof(double)));
+    cudaError_t e = cudaMallocHost(&hh, n * sizeof(double));
     if (e != cudaSuccess) {
       cudaFree(h);
       return fail(CBS_ERR_CUDA, "cudaMallocHost: %s", cudaGetErrorString(e));
@@ -858,6 +929,7 @@ int cbs_set_solver(cbs_plan_t p, double tol, int max_iter, int check_every) {
     p->hist = h;
     p->hist_host = hh;
     p->base.hist = h;
+    p->base.hist_cap = check_every;
   }
   p->d.tol = tol;
   p->d.max_iter = max_iter;
@@ -878,40 +950,13 @@ int cbs_set_permittivity(cbs_plan_t p, const float* eps) {
   g_err.clear();
   if (!p || !eps) return fail(CBS_ERR_ARG, "NULL argument");
   int rc = sync_in(p);
+  if (!rc) rc = seat_permittivity(p, 0, eps, p->stream);
   if (rc) return rc;
-  const int B = p->red_blocks;
-  CK(launch_eps_minmax(eps, p->N, p->pmin, p->pmax, p->pbad, B, p->stream));
-  std::vector<float> mn(B), mx(B);
-  std::vector<int> bad(B);
-  CK(cudaMemcpyAsync(mn.data(), p->pmin, B * sizeof(float), cudaMemcpyDeviceToHost, p->stream));
-  CK(cudaMemcpyAsync(mx.data(), p->pmax, B * sizeof(float), cudaMemcpyDeviceToHost, p->stream));
-  CK(cudaMemcpyAsync(bad.data(), p->pbad, B * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
-  CK(cudaStreamSynchronize(p->stream));
-  double lo = 1e300, hi = -1e300;
-  for (int b = 0; b < B; ++b) {
-    if (bad[b]) return fail(CBS_ERR_ARG, "permittivity contains a non-finite value");
-    lo = std::min(lo, (double)mn[b]);
-    hi = std::max(hi, (double)mx[b]);
-  }
-  const double kv2 = (p->kvac * p->pitch) * (p->kvac * p->pitch);
-  const double k0sq = 0.5 * kv2 * (lo + hi);
-  CK(launch_k2_maxdev(eps, p->d.nx, p->d.ny, p->d.nz, p->sx, p->sy, p->sz, p->layers.corner_max, kv2, k0sq,
-                      p->pdev, B, p->stream));
-  std::vector<double> dv(B);
-  CK(cudaMemcpyAsync(dv.data(), p->pdev, B * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
-  CK(cudaStreamSynchronize(p->stream));
-  double epsilon = 0.0;
-  for (int b = 0; b < B; ++b) epsilon = std::max(epsilon, dv[b]);
-  if (!(epsilon > 0.0) || !std::isfinite(epsilon))
-    return fail(CBS_ERR_ARG, "epsilon = %g: a lossless homogeneous grid has no convergent splitting", epsilon);
-  CK(launch_build_v(eps, p->d.nx, p->d.ny, p->d.nz, p->base.nxp, p->base.yblk, p->sx, p->sy, p->sz, p->layers.corner_max, kv2,
-                    k0sq, epsilon, p->V, p->stream));
-  CK(cudaStreamSynchronize(p->stream));
-  p->k0sq_s = k0sq;
-  p->eps_s = epsilon;
-  IterArgs& a = p->base;
-  a.inv_eps = (float)(1.0 / epsilon);
-  a.kt2 = make_float2((float)k0sq, (float)epsilon);
+  p->k0sq_s = p->seat_k0sq[0];
+  p->eps_s = p->seat_eps[0];
+  Member& m = p->base.mem[0];
+  m.inv_eps = (float)(1.0 / p->eps_s);
+  m.kt2 = make_float2((float)p->k0sq_s, (float)p->eps_s);
   p->have_eps = true;
   drop_graphs(p);   // kernel parameters changed
   return CBS_OK;

@@ -21,6 +21,20 @@ struct SourceArgs {
   float user_scale;       // pitch^2
 };
 
+// Requests that share one launch: a plan's arrays (E, W, V) hold `seats` requests of the same
+// grid side by side, and a launch iterates up to kMaxMembers of them, each with its own source
+// and splitting.  A launch's grid is nmem times the per-request persistent grid; block b works
+// for member b / grid, as block b mod grid of that request's own persistent grid, so every
+// request's tiles, and the order of its residual sums, are the same in any launch.
+constexpr int kMaxMembers = 8;
+
+struct Member {
+  SourceArgs src;
+  float inv_eps;          // 1 / epsilon (scaled)
+  float2 kt2;             // k0^2 + i epsilon (scaled)
+  int seat;               // slice of the plan's arrays: E, W at + seat * 3 Nw; V at + seat * Nw
+};
+
 // Everything one CBS iteration needs (kernel parameters, by value).
 struct IterArgs {
   int nx, ny, nz;
@@ -39,16 +53,17 @@ struct IterArgs {
   const float2* pqy;      // padded with zeros to a multiple of 16 entries
   const float2* pqz;
   int pqbz;               // bytes of the z table the z pass copies (multiple of 16)
-  float2* E;              // field being iterated, [3][nyb][nz][yblk][nxp] (plan-owned copy)
+  float2* E;              // fields being iterated, [seats][3][nyb][nz][yblk][nxp] (plan-owned)
   float2* W;              // workspace, same layout
-  const float2* V;        // potential [nyb][nz][yblk][nxp], scaled
-  SourceArgs src;
-  float inv_eps;          // 1 / epsilon (scaled)
-  float2 kt2;             // k0^2 + i epsilon (scaled)
+  const float2* V;        // potential [seats][nyb][nz][yblk][nxp], scaled
+  int seats;              // requests the arrays hold
+  int nmem;               // members of this launch (1 .. kMaxMembers)
+  Member mem[kMaxMembers];
   float invN;             // 1 / N, folded into the k-space multiply
-  double* partials;       // per-block residual partial sums
-  unsigned* counter;      // last-block-done counter (left at 0)
-  double* hist;           // hist[slot] = sum |delta|^2 of this iteration
+  double* partials;       // residual partial sums, [seat][grid_x]
+  unsigned* counter;      // last-block-done counters, [seat] (left at 0)
+  double* hist;           // hist[seat * hist_cap + slot] = sum |delta|^2 of this iteration
+  int hist_cap;
   int slot;
   int* err;               // device error flag (a tensor-copy wait that timed out)
   // launch shapes
@@ -59,8 +74,18 @@ struct IterArgs {
   int occ_y, occ_z;       // blocks per SM of the y and z kernels (2: radices <= 11, 64 registers)
   int maxr_x, maxr_z;     // largest radix of the x and z axes (selects the kernel build)
   int xgroups, zgroups;   // warp groups of the fused x and the z blocks (1 or 2)
-  int grid_x, grid_xf, grid_y, grid_z;   // persistent grid sizes (x inverse, x forward, y, z)
+  int grid_x, grid_xf, grid_y, grid_z;   // persistent grid sizes of one request (x inverse,
+                                         // x forward, y, z); a launch has nmem times as many
 };
+
+// Block b of a launch: member b / G, block b mod G of that member's grid of G blocks.
+struct MemberBlock {
+  int j, b;
+};
+CBS_HD MemberBlock member_block(int block, int G) {
+  const int j = block / G;
+  return MemberBlock{j, block - j * G};
+}
 
 // The plan's arrays (W, the iterate E, V) store row (y, z) of a component at
 //     ((y / yblk) * nz + z) * yblk + y mod yblk

@@ -64,6 +64,7 @@ struct cbs_plan_s {
   int* err_dev = nullptr;          // kernels' error flag
   int* err_host = nullptr;         // pinned copy
   cbs::IterArgs base{};
+  int seats = 1;                   // requests the arrays hold side by side (cbs_plan: 1)
   size_t N = 0;
   double pitch = 0, kvac = 0;
   cbs::LayerSpec layers{};         // absorbing-layer profile (absorber.h)
@@ -94,9 +95,10 @@ struct cbs_plan_s {
   float2* Ef = nullptr;
   float2* Ea = nullptr;
   float* grad_dev = nullptr;
-  // splitting (scaled units)
+  // splitting (scaled units) of the plan's own solves (seat 0), and of every seat
   bool have_eps = false;
   double k0sq_s = 0, eps_s = 0;
+  std::vector<double> seat_k0sq, seat_eps;
   // graphs of one block of check_every iterations, per (E, source) binding
   std::vector<cbs::GraphEntry> graphs;
   // pass timing (events around the launches of the last iteration of each block)
@@ -125,12 +127,22 @@ struct SeriesRun {
   std::chrono::steady_clock::time_point t0;
 };
 
+// Plans with several seats and their set-up (api.cu).
+int plan_create(cbs_plan_s** out, const cbs_plan_desc* desc, int seats);
+int seat_permittivity(cbs_plan_s* p, int seat, const float* eps, cudaStream_t s);
+cudaError_t field_copy(const cbs_plan_s* p, int seat, float2* dense, bool to_dense, cudaStream_t s);
+// The launches of one iteration after a series' first, for the members in a (api.cu).
+int launch_iteration(const cbs_plan_s* p, const IterArgs& a, cudaStream_t s, cudaEvent_t* ev);
+
 // Series driver (api.cu).
 int sync_in(cbs_plan_s* p);
 int make_source(cbs_plan_s* p, const cbs_source* src, SourceArgs& s);
 void series_begin(cbs_plan_s* p, float2* E, const SourceArgs& src, int warm, SeriesRun& R);
 bool series_advance(cbs_plan_s* p, SeriesRun& R, bool wait);
 int series_stats(const cbs_plan_s* p, SeriesRun& R, cbs_stats* S);
+// The stopping rules on the residual sums h[0 .. R.m-1] of a block (sets R.rc on an error);
+// returns whether the run is over.
+bool series_absorb_residuals(const cbs_plan_s* p, SeriesRun& R, const double* h);
 int run_series(cbs_plan_s* p, float2* E, const SourceArgs& src, int warm, cbs_stats* st);
 // Source of the adjoint of |E(r0)|^2 (enqueues the read of conj(E(r0)) on the plan's stream).
 int adjoint_source(cbs_plan_s* p, const int r0[3], const void* E_dev, SourceArgs& s);

@@ -28,12 +28,15 @@ namespace cbs {
 
 namespace {
 
-__device__ __forceinline__ float2 source_at(const IterArgs& a, int c, int z, int y, int x) {
-  const SourceArgs& s = a.src;
-  if (s.kind == 0) {
-    if (z == s.zp) return s.amp[c];
-  } else if (s.kind == 1) {
-    if (z == s.pz && y == s.py && x == s.px) return s.amp_dev ? s.amp_dev[c] : s.amp[c];
+// The source of component c at voxel (x, y, z); kind and plane (the sheet's z, or the point's
+// z) are s.kind and s.zp / s.pz, read once into registers by the caller (s itself sits in the
+// launch's parameters at a member index known only at run time).
+__device__ __forceinline__ float2 source_at(const IterArgs& a, const SourceArgs& s, int kind, int plane, int c,
+                                            int z, int y, int x) {
+  if (kind == 0) {
+    if (z == plane) return s.amp[c];
+  } else if (kind == 1) {
+    if (z == plane && y == s.py && x == s.px) return s.amp_dev ? s.amp_dev[c] : s.amp[c];
   } else {
     const size_t idx = ((size_t)z * a.ny + y) * a.nx + x;   // the caller's dense layout
     return cscale(__ldg(&s.user[c * a.N + idx]), s.user_scale);
@@ -42,8 +45,12 @@ __device__ __forceinline__ float2 source_at(const IterArgs& a, int c, int z, int
 }
 
 // Block reduction of the per-thread residual in FP64, then a last-block-done pass that sums
-// the per-block partials in a fixed order into hist[slot] (deterministic).
-__device__ __forceinline__ void residual_finish(float acc, const IterArgs& a, double* wsum, int* lastflag) {
+// the per-block partials of the request in seat `seat` (blocks b = 0 .. G-1 of its grid) in a
+// fixed order into its hist[slot] (deterministic).
+__device__ __forceinline__ void residual_finish(float acc, const IterArgs& a, int seat, int b, int G, double* wsum,
+                                                int* lastflag) {
+  double* const part = a.partials + (size_t)seat * a.grid_x;
+  unsigned* const counter = a.counter + seat;
   double d = (double)acc;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) d += __shfl_down_sync(0xffffffffu, d, off);
@@ -52,28 +59,28 @@ __device__ __forceinline__ void residual_finish(float acc, const IterArgs& a, do
   if (lane == 0) wsum[wid] = d;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double b = 0.0;
-    for (int w = 0; w < nw; ++w) b += wsum[w];
-    a.partials[blockIdx.x] = b;
+    double bs = 0.0;
+    for (int w = 0; w < nw; ++w) bs += wsum[w];
+    part[b] = bs;
     __threadfence();
-    const unsigned prev = atomicAdd(a.counter, 1u);
-    *lastflag = (prev == gridDim.x - 1);
+    const unsigned prev = atomicAdd(counter, 1u);
+    *lastflag = (prev == (unsigned)G - 1);
   }
   __syncthreads();
   if (!*lastflag) return;
   __threadfence();
   double s = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s += __ldcg(&a.partials[i]);
+  for (int i = threadIdx.x; i < G; i += blockDim.x) s += __ldcg(&part[i]);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
   __syncthreads();
   if (lane == 0) wsum[wid] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double b = 0.0;
-    for (int w = 0; w < nw; ++w) b += wsum[w];
-    a.hist[a.slot] = b;
-    *a.counter = 0u;
+    double bs = 0.0;
+    for (int w = 0; w < nw; ++w) bs += wsum[w];
+    a.hist[(size_t)seat * a.hist_cap + a.slot] = bs;
+    *counter = 0u;
   }
 }
 
@@ -166,35 +173,42 @@ __device__ __forceinline__ void row_stages(float2* buf, int cs, int ld, int nr, 
 // Persistent forward x pass (a series' first iteration): V E + S formed as the first stage
 // loads each element, transformed in place in the E buffer, stored as W.
 template <int MAXR>
-__global__ void __launch_bounds__(kThreads, kXOcc) k_xpass_fwd(const IterArgs a) {
+__global__ void __launch_bounds__(kThreads, kXOcc) k_xpass_fwd(const __grid_constant__ IterArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int rpb = a.rpb, nxp = a.nxp, nset = a.nset_xf;
   const int span = rpb * nxp;
   const int rows = a.ny * a.nz, ntiles = x_tiles(a);
+  const int G = a.grid_xf;
+  const MemberBlock mb = member_block(blockIdx.x, G);
+  const Member& mem = a.mem[mb.j];
+  const size_t so = (size_t)mem.seat * 3 * a.Nw;
+  const float2* const E = a.E + so;
+  float2* const W = a.W + so;
+  const float2* const V = a.V + (size_t)mem.seat * a.Nw;
+  const int skind = mem.src.kind, splane = skind == 1 ? mem.src.pz : mem.src.zp;
   XTile t = carve(smem_raw, rpb, nxp, a.twbx, nset, 4);
-  if ((int)blockIdx.x >= ntiles) return;
+  if (mb.b >= ntiles) return;
   if (!block_setup_n(t.set0, t.full, nset, t.fail, a.err)) return;
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int G = gridDim.x;
   const RowDecode rowdec = row_decode(a);
   auto issue = [&](int tt, int k, uint32_t extra) {
     const int r0 = tt * rpb, nr = min(rpb, rows - r0);
     const uint32_t bytes = (uint32_t)(nr * nxp * sizeof(float2));
     float2* s = t.set0 + k * t.set;
     mbar_arrive_expect_tx(&t.full[k], 4 * bytes + extra);
-    for (int c = 0; c < 3; ++c) bulk_load(s + c * span, a.E + c * a.Nw + (size_t)r0 * nxp, bytes, &t.full[k]);
-    bulk_load(s + 3 * span, a.V + (size_t)r0 * nxp, bytes, &t.full[k]);
+    for (int c = 0; c < 3; ++c) bulk_load(s + c * span, E + c * a.Nw + (size_t)r0 * nxp, bytes, &t.full[k]);
+    bulk_load(s + 3 * span, V + (size_t)r0 * nxp, bytes, &t.full[k]);
   };
   if (tid == 0) {
-    issue(blockIdx.x, 0, a.twbx);
+    issue(mb.b, 0, a.twbx);
     bulk_load(t.tw, a.twx, a.twbx, &t.full[0]);
     for (int d = 1; d < nset - 1; ++d)
-      if ((int)blockIdx.x + d * G < ntiles) issue(blockIdx.x + d * G, d, 0);
+      if (mb.b + d * G < ntiles) issue(mb.b + d * G, d, 0);
   }
   const int ns = a.ax.ns;
   const IPStage s0 = ip_decode_stage(a.ax, 0);
   int k = 0;
-  for (int i = 0, tile = blockIdx.x; tile < ntiles; ++i, tile += G, k = (k + 1 == nset) ? 0 : k + 1) {
+  for (int i = 0, tile = mb.b; tile < ntiles; ++i, tile += G, k = (k + 1 == nset) ? 0 : k + 1) {
     const int r0 = tile * rpb, nr = min(rpb, rows - r0);
     if (!block_wait(&t.full[k], t.fail, a.err, (uint32_t)((i / nset) & 1))) return;
     float2* e = t.set0 + k * t.set;
@@ -210,7 +224,7 @@ __global__ void __launch_bounds__(kThreads, kXOcc) k_xpass_fwd(const IterArgs a)
       const int gr = r0 + row;
       int y, z;
       rowdec(gr, y, z);
-      return cadd(cmul(v[row * nxp + x], ev), source_at(a, c, z, y, x));
+      return cadd(cmul(v[row * nxp + x], ev), source_at(a, mem.src, skind, splane, c, z, y, x));
     };
     radix_dispatch<MAXR>(s0.R, [&](auto Ri) {
       constexpr int R = decltype(Ri)::value;
@@ -226,7 +240,7 @@ __global__ void __launch_bounds__(kThreads, kXOcc) k_xpass_fwd(const IterArgs a)
     __syncthreads();
     if (tid == 0) {
       const uint32_t bytes = (uint32_t)(nr * nxp * sizeof(float2));
-      for (int c = 0; c < 3; ++c) bulk_store(a.W + c * a.Nw + (size_t)r0 * nxp, e + c * span, bytes);
+      for (int c = 0; c < 3; ++c) bulk_store(W + c * a.Nw + (size_t)r0 * nxp, e + c * span, bytes);
       bulk_commit();
     }
   }
@@ -245,17 +259,24 @@ __global__ void __launch_bounds__(kThreads, kXOcc) k_xpass_fwd(const IterArgs a)
 // A group whose copy wait times out records the error and stops taking tiles, but still
 // joins the block's final residual reduction.
 template <int MAXR>
-__global__ void __launch_bounds__(kThreads, kXOcc) k_xpass_inv_fwd(const IterArgs a) {
+__global__ void __launch_bounds__(kThreads, kXOcc) k_xpass_inv_fwd(const __grid_constant__ IterArgs a) {
   const int NG = a.xgroups, GT = kThreads / NG;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int rpb = a.rpb, nxp = a.nxp, nset = a.nset_x;
   const int span = rpb * nxp;
   const int rows = a.ny * a.nz, ntiles = x_tiles(a);
+  const int G = a.grid_x;
+  const MemberBlock mb = member_block(blockIdx.x, G);
+  const Member& mem = a.mem[mb.j];
+  const size_t so = (size_t)mem.seat * 3 * a.Nw;
+  float2* const E = a.E + so;
+  float2* const W = a.W + so;
+  const float2* const V = a.V + (size_t)mem.seat * a.Nw;
+  const int skind = mem.src.kind, splane = skind == 1 ? mem.src.pz : mem.src.zp;
   XTile t = carve(smem_raw, rpb, nxp, a.twbx, nset, 7);
   float acc = 0.f;
   const int tid = threadIdx.x, g = tid / GT, lt = tid - g * GT;
-  const int G = gridDim.x;
-  if ((int)blockIdx.x < ntiles) {
+  if (mb.b < ntiles) {
     if (tid == 0) t.fail[1] = 0;
     if (!block_setup_n(t.set0, t.full, nset + 1, t.fail, a.err)) return;   // also clears fail[0]
     auto issue = [&](int tt, int k) {
@@ -264,17 +285,17 @@ __global__ void __launch_bounds__(kThreads, kXOcc) k_xpass_inv_fwd(const IterArg
       float2* s = t.set0 + k * t.set;
       mbar_arrive_expect_tx(&t.full[k], 7 * bytes);
       for (int c = 0; c < 3; ++c) {
-        bulk_load(s + c * span, a.W + c * a.Nw + (size_t)r0 * nxp, bytes, &t.full[k]);
-        bulk_load(s + (3 + c) * span, a.E + c * a.Nw + (size_t)r0 * nxp, bytes, &t.full[k]);
+        bulk_load(s + c * span, W + c * a.Nw + (size_t)r0 * nxp, bytes, &t.full[k]);
+        bulk_load(s + (3 + c) * span, E + c * a.Nw + (size_t)r0 * nxp, bytes, &t.full[k]);
       }
-      bulk_load(s + 6 * span, a.V + (size_t)r0 * nxp, bytes, &t.full[k]);
+      bulk_load(s + 6 * span, V + (size_t)r0 * nxp, bytes, &t.full[k]);
     };
     const int D = nset - NG;   // prefetch distance in tiles
     if (tid == 0) {
       mbar_arrive_expect_tx(t.tbar, a.twbx);
       bulk_load(t.tw, a.twx, a.twbx, t.tbar);
       for (int d = 0; d < D; ++d)
-        if ((int)blockIdx.x + d * G < ntiles) issue(blockIdx.x + d * G, d);
+        if (mb.b + d * G < ntiles) issue(mb.b + d * G, d);
     }
     auto gsync = [&] {
       if (NG == 1) __syncthreads();
@@ -289,12 +310,12 @@ __global__ void __launch_bounds__(kThreads, kXOcc) k_xpass_inv_fwd(const IterArg
       }
       return true;
     };
-    const float ie = a.inv_eps;
+    const float ie = mem.inv_eps;
     const RowDecode rowdec = row_decode(a);
     const int ns = a.ax.ns;
     const IPStage s0 = ip_decode_stage(a.ax, 0);
     bool ok = gwait(t.tbar, 0);
-    for (int i = g, tile = blockIdx.x + g * G; ok && tile < ntiles; i += NG, tile += NG * G) {
+    for (int i = g, tile = mb.b + g * G; ok && tile < ntiles; i += NG, tile += NG * G) {
       const int k = i % nset;
       const int r0 = tile * rpb, nr = min(rpb, rows - r0);
       if (!gwait(&t.full[k], (uint32_t)((i / nset) & 1))) {
@@ -327,7 +348,7 @@ __global__ void __launch_bounds__(kThreads, kXOcc) k_xpass_inv_fwd(const IterArg
         acc = fmaf(d.x, d.x, fmaf(d.y, d.y, acc));
         int y, z;
         rowdec(r0 + row, y, z);
-        return cadd(cmul(vv, en), source_at(a, c, z, y, x));
+        return cadd(cmul(vv, en), source_at(a, mem.src, skind, splane, c, z, y, x));
       };
       radix_dispatch<MAXR>(s0.R, [&](auto Ri) {
         constexpr int R = decltype(Ri)::value;
@@ -341,19 +362,19 @@ __global__ void __launch_bounds__(kThreads, kXOcc) k_xpass_inv_fwd(const IterArg
       if (ns == 1) prefetch();
       const uint32_t bytes = (uint32_t)(nr * nxp * sizeof(float2));
       if (lt == 0) {
-        for (int c = 0; c < 3; ++c) bulk_store(a.E + c * a.Nw + (size_t)r0 * nxp, e + c * span, bytes);
+        for (int c = 0; c < 3; ++c) bulk_store(E + c * a.Nw + (size_t)r0 * nxp, e + c * span, bytes);
         bulk_commit();
       }
       row_stages<false, MAXR>(w, span, nxp, nr, a.ax, 1, ns, t.tw, lt, GT, NoHookIP{}, gsync);
       fence_async_smem();
       gsync();
       if (lt == 0) {
-        for (int c = 0; c < 3; ++c) bulk_store(a.W + c * a.Nw + (size_t)r0 * nxp, w + c * span, bytes);
+        for (int c = 0; c < 3; ++c) bulk_store(W + c * a.Nw + (size_t)r0 * nxp, w + c * span, bytes);
         bulk_commit();
       }
     }
   }
-  residual_finish(acc, a, t.wsum, t.last);
+  residual_finish(acc, a, mem.seat, mb.b, G, t.wsum, t.last);
   if (lt == 0) bulk_wait_all();
 }
 
@@ -396,7 +417,7 @@ cudaError_t x_grid_size(IterArgs& a, int sms) {
 cudaError_t launch_xpass_fwd(const IterArgs& a, cudaStream_t s) {
   return with_maxr_x(a.maxr_x, [&](auto M) {
     constexpr int MR = decltype(M)::value;
-    k_xpass_fwd<MR><<<a.grid_xf, kThreads, xpass_fwd_smem(a), s>>>(a);
+    k_xpass_fwd<MR><<<a.grid_xf * a.nmem, kThreads, xpass_fwd_smem(a), s>>>(a);
     return cudaGetLastError();
   });
 }
@@ -404,7 +425,7 @@ cudaError_t launch_xpass_fwd(const IterArgs& a, cudaStream_t s) {
 cudaError_t launch_xpass_inv_fwd(const IterArgs& a, cudaStream_t s) {
   return with_maxr_x(a.maxr_x, [&](auto M) {
     constexpr int MR = decltype(M)::value;
-    k_xpass_inv_fwd<MR><<<a.grid_x, kThreads, xpass_smem(a), s>>>(a);
+    k_xpass_inv_fwd<MR><<<a.grid_x * a.nmem, kThreads, xpass_smem(a), s>>>(a);
     return cudaGetLastError();
   });
 }

@@ -105,14 +105,15 @@ __device__ __forceinline__ void col_stages(float2* buf, int cs, const AxisIP& ap
   }
 }
 
-// Persistent y pass: a block walks tiles t = blockIdx.x, + gridDim.x, ... through nbuf tile
-// buffers.  Tile i is transformed in buffer i mod nbuf; after its first stage, thread 0 issues
+// Persistent y pass: block b of a request's grid of G blocks walks the request's tiles
+// t = b, b + G, ... through nbuf tile buffers.  Tile i is transformed in buffer i mod nbuf; after its first stage, thread 0 issues
 // the copies of tile i + nbuf - 1 into the buffer of tile i - 1 (once that tile's store has
 // been read out of it).  OCC blocks per SM: 1 (512 threads, up to 128 registers, all radices)
 // or 2 (256 threads each, radices up to MAXR = 11; two independent blocks keep issuing while
 // the other waits at a barrier).
 template <int TX, bool INV, int OCC>
-__global__ void __launch_bounds__(y_threads<OCC>(), OCC) k_ypass(const __grid_constant__ CUtensorMap tm, const IterArgs a) {
+__global__ void __launch_bounds__(y_threads<OCC>(), OCC) k_ypass(const __grid_constant__ CUtensorMap tm,
+                                                                const __grid_constant__ IterArgs a) {
   constexpr int MAXR = OCC == 1 ? 16 : 11;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int tileN = a.nyr * TX, nbuf = a.nbuf_y;
@@ -124,24 +125,27 @@ __global__ void __launch_bounds__(y_threads<OCC>(), OCC) k_ypass(const __grid_co
   const int ntiles = nxt * a.nz * 3;
   const int B = a.yb, nbox = a.nyr / B;
   const uint32_t tile_bytes = (uint32_t)(nbox * B * TX * sizeof(float2));
-  if ((int)blockIdx.x >= ntiles) return;
+  const int G = a.grid_y;
+  const MemberBlock mb = member_block(blockIdx.x, G);
+  const int c0 = 3 * a.mem[mb.j].seat;   // the request's first component in the tensor map
+  if (mb.b >= ntiles) return;
   if (!block_setup_n(buf0, full, nbuf, fail, a.err)) return;
   auto issue = [&](int tt, int bb, uint32_t extra) {
     mbar_arrive_expect_tx(&full[bb], tile_bytes + extra);
     const int xt = tt % nxt, r = tt / nxt;
     const int z = r % a.nz, c = r / a.nz;
-    for (int b = 0; b < nbox; ++b) tma_load_5d(buf0 + bb * tileN + b * B * TX, &tm, xt * TX, 0, z, b, c, &full[bb]);
+    for (int b = 0; b < nbox; ++b)
+      tma_load_5d(buf0 + bb * tileN + b * B * TX, &tm, xt * TX, 0, z, b, c0 + c, &full[bb]);
   };
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int G = gridDim.x;
   if (tid == 0) {
-    issue(blockIdx.x, 0, a.twby);   // the first tile's barrier also counts the twiddles
+    issue(mb.b, 0, a.twby);   // the first tile's barrier also counts the twiddles
     bulk_load(tw, a.twy, a.twby, &full[0]);
     for (int d = 1; d < nbuf - 1; ++d)
-      if ((int)blockIdx.x + d * G < ntiles) issue(blockIdx.x + d * G, d, 0);
+      if (mb.b + d * G < ntiles) issue(mb.b + d * G, d, 0);
   }
   int b = 0;
-  for (int i = 0, t = blockIdx.x; t < ntiles; ++i, t += G, b = (b + 1 == nbuf) ? 0 : b + 1) {
+  for (int i = 0, t = mb.b; t < ntiles; ++i, t += G, b = (b + 1 == nbuf) ? 0 : b + 1) {
     float2* cur = buf0 + b * tileN;
     if (!block_wait(&full[b], fail, a.err, (uint32_t)((i / nbuf) & 1))) return;
     auto prefetch = [&] {
@@ -158,7 +162,7 @@ __global__ void __launch_bounds__(y_threads<OCC>(), OCC) k_ypass(const __grid_co
     if (tid == 0) {
       const int xt = t % nxt, r = t / nxt;
       const int z = r % a.nz, c = r / a.nz;
-      for (int bx = 0; bx < nbox; ++bx) tma_store_5d(&tm, xt * TX, 0, z, bx, c, cur + bx * B * TX);
+      for (int bx = 0; bx < nbox; ++bx) tma_store_5d(&tm, xt * TX, 0, z, bx, c0 + c, cur + bx * B * TX);
       bulk_commit();
     }
   }
@@ -183,7 +187,8 @@ __device__ __forceinline__ void group_sync(int id, int count) {
 // wave-number tables have their own barrier.
 template <int TX, int MAXR>
 __global__ void __launch_bounds__(kZThreads, kZOcc) k_zpass_green(const __grid_constant__ CUtensorMap tm,
-                                                               const IterArgs a) {
+                                                               const __grid_constant__ IterArgs a) {
+  static_assert(kZThreads % (2 * TX) == 0, "a warp group's threads must be a multiple of the tile width");
   const int NG = a.zgroups, GT = kZThreads / NG;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int nzr = a.nzr;
@@ -198,8 +203,11 @@ __global__ void __launch_bounds__(kZThreads, kZOcc) k_zpass_green(const __grid_c
   const int ntiles = nxt * a.ny;
   const int B = a.zb, nbox = nzr / B;
   const uint32_t tile_bytes = (uint32_t)(3 * nbox * B * TX * sizeof(float2));
-  const int G = gridDim.x;
-  if ((int)blockIdx.x >= ntiles) return;
+  const int G = a.grid_z;
+  const MemberBlock mb = member_block(blockIdx.x, G);
+  const int c0 = 3 * a.mem[mb.j].seat;   // the request's first component in the tensor map
+  const float2 kt2 = a.mem[mb.j].kt2;
+  if (mb.b >= ntiles) return;
   const int tid = threadIdx.x, g = tid / GT, lt = tid - g * GT;
   if (tid == 0) fail[1] = 0;
   if (!block_setup_n(buf0, full, nbuf + 1, fail, a.err)) return;   // also clears fail[0]
@@ -209,7 +217,7 @@ __global__ void __launch_bounds__(kZThreads, kZOcc) k_zpass_green(const __grid_c
     const int yb = y / a.yblk, yi = y - yb * a.yblk;
     for (int c = 0; c < 3; ++c)
       for (int b = 0; b < nbox; ++b)
-        tma_load_5d(buf0 + bb * tileN + (c * nzr + b * B) * TX, &tm, xt * TX, yi, b * B, yb, c, &full[bb]);
+        tma_load_5d(buf0 + bb * tileN + (c * nzr + b * B) * TX, &tm, xt * TX, yi, b * B, yb, c0 + c, &full[bb]);
   };
   const int D = nbuf - NG;   // prefetch distance in tiles
   if (tid == 0) {
@@ -217,7 +225,7 @@ __global__ void __launch_bounds__(kZThreads, kZOcc) k_zpass_green(const __grid_c
     bulk_load(tw, a.twz, a.twbz, tbar);
     bulk_load(pqz, a.pqz, a.pqbz, tbar);
     for (int d = 0; d < D; ++d)
-      if ((int)blockIdx.x + d * G < ntiles) issue(blockIdx.x + d * G, d);
+      if (mb.b + d * G < ntiles) issue(mb.b + d * G, d);
   }
   auto gsync = [&] {
     if (NG == 1) __syncthreads();
@@ -236,7 +244,7 @@ __global__ void __launch_bounds__(kZThreads, kZOcc) k_zpass_green(const __grid_c
   if (!gwait(tbar, 0)) return;
   const int ns = a.az.ns;
   const IPStage sl = ip_decode_stage(a.az, ns - 1);
-  for (int i = g, t = blockIdx.x + g * G; t < ntiles; i += NG, t += NG * G) {
+  for (int i = g, t = mb.b + g * G; t < ntiles; i += NG, t += NG * G) {
     const int b = i % nbuf;
     float2* cur = buf0 + b * tileN;
     if (!gwait(&full[b], (uint32_t)((i / nbuf) & 1))) return;
@@ -250,13 +258,16 @@ __global__ void __launch_bounds__(kZThreads, kZOcc) k_zpass_green(const __grid_c
     const int xt = t % nxt, y = t / nxt;
     const int x0 = xt * TX;
     const float2 pqy = __ldg(&a.pqy[y]);
+    // the fused stage gives thread lt the items lt, lt + GT, ...: all in column lt mod TX, as
+    // GT is a multiple of TX; so its x wave number is read once per tile (the table is padded
+    // past nx)
+    const float2 px = __ldg(&a.pqx[x0 + lt % TX]);
     col_stages<false, TX, 3, MAXR, true>(cur, cs, a.az, 0, ns - 1, tw, lt, GT, prefetch, gsync);
     radix_dispatch<MAXR>(sl.R, [&](auto Ri) {
       constexpr int R = decltype(Ri)::value;
-      ipz_fused<R, TX>(cur, cs, sl, lt, GT, [&](int col, int pos, float2& X0, float2& X1, float2& X2) {
-        const float2 px = __ldg(&a.pqx[x0 + col]);   // the table is padded past nx
+      ipz_fused<R, TX>(cur, cs, sl, lt, GT, [&](int, int pos, float2& X0, float2& X1, float2& X2) {
         const float2 pz = pqz[pos];
-        green(px.x, pqy.x, pz.x, px.y, pqy.y, pz.y, a.kt2, a.invN, X0, X1, X2);
+        green(px.x, pqy.x, pz.x, px.y, pqy.y, pz.y, kt2, a.invN, X0, X1, X2);
       });
     });
     gsync();
@@ -267,7 +278,8 @@ __global__ void __launch_bounds__(kZThreads, kZOcc) k_zpass_green(const __grid_c
     if (lt == 0) {
       const int yb = y / a.yblk, yi = y - yb * a.yblk;
       for (int c = 0; c < 3; ++c)
-        for (int bb = 0; bb < nbox; ++bb) tma_store_5d(&tm, x0, yi, bb * B, yb, c, cur + (c * nzr + bb * B) * TX);
+        for (int bb = 0; bb < nbox; ++bb)
+          tma_store_5d(&tm, x0, yi, bb * B, yb, c0 + c, cur + (c * nzr + bb * B) * TX);
       bulk_commit();
     }
   }
@@ -298,11 +310,11 @@ template <int TX>
 cudaError_t y_launch(const CUtensorMap& tm, const IterArgs& a, bool inverse, cudaStream_t s) {
   const size_t sm = ypass_smem(a);
   if (a.occ_y == 2) {
-    if (inverse) yzk::k_ypass<TX, true, 2><<<a.grid_y, yzk::kY2Threads, sm, s>>>(tm, a);
-    else yzk::k_ypass<TX, false, 2><<<a.grid_y, yzk::kY2Threads, sm, s>>>(tm, a);
+    if (inverse) yzk::k_ypass<TX, true, 2><<<a.grid_y * a.nmem, yzk::kY2Threads, sm, s>>>(tm, a);
+    else yzk::k_ypass<TX, false, 2><<<a.grid_y * a.nmem, yzk::kY2Threads, sm, s>>>(tm, a);
   } else {
-    if (inverse) yzk::k_ypass<TX, true, 1><<<a.grid_y, yzk::kYThreads, sm, s>>>(tm, a);
-    else yzk::k_ypass<TX, false, 1><<<a.grid_y, yzk::kYThreads, sm, s>>>(tm, a);
+    if (inverse) yzk::k_ypass<TX, true, 1><<<a.grid_y * a.nmem, yzk::kYThreads, sm, s>>>(tm, a);
+    else yzk::k_ypass<TX, false, 1><<<a.grid_y * a.nmem, yzk::kYThreads, sm, s>>>(tm, a);
   }
   return cudaGetLastError();
 }
@@ -332,7 +344,7 @@ cudaError_t z_occupancy(const IterArgs& a, int* occ) {
 template <int TX>
 cudaError_t z_launch(const CUtensorMap& tm, const IterArgs& a, cudaStream_t s) {
   return z_with_maxr<TX>(a.maxr_z, [&](auto k) {
-    k<<<a.grid_z, yzk::kZThreads, zpass_smem(a), s>>>(tm, a);
+    k<<<a.grid_z * a.nmem, yzk::kZThreads, zpass_smem(a), s>>>(tm, a);
     return cudaGetLastError();
   });
 }

@@ -168,17 +168,20 @@ SEED_STREAM = 42
 
 
 def serving_stream(n: int, sizes=SERVING_SIZES, seed: int = SEED_STREAM, ppl: int = 8, lam: float = 1.064e-6,
-                   p_adjoint: float = 0.5, rate_hz: float | None = None) -> list:
+                   p_adjoint: float = 0.5, rate_hz: float | None = None, balanced: bool = False) -> list:
     """Seeded request mix: grid uniform over `sizes` at pitch lam / ppl with one-wavelength
     absorbing layers on every face, a centred sphere (radius 1.5 um or 0.3 of the interior,
     the smaller) or a Fresnel lens (D = 0.7 of the lateral interior), equal odds, of index
     U[1.3, 1.6], an x-polarised plane wave, forward only or forward + adjoint (p_adjoint).
-    Each request is a dict; arrivals (Poisson, rate_hz) are added when rate_hz is given."""
+    balanced: every size equally often (n // len(sizes) or one more), in random order, so that
+    a short stream still covers every size.  Each request is a dict; arrivals (Poisson,
+    rate_hz) are added when rate_hz is given."""
     rng = np.random.default_rng(seed)
     pitch = lam / ppl
+    order = rng.permutation(np.resize(np.arange(len(sizes)), n)) if balanced else None
     out = []
     for i in range(n):
-        nx, ny, nz = sizes[int(rng.integers(len(sizes)))]
+        nx, ny, nz = sizes[int(order[i] if balanced else rng.integers(len(sizes)))]
         kind = "sphere" if rng.random() < 0.5 else "lens"
         n_idx = float(rng.uniform(1.3, 1.6))
         adj = bool(rng.random() < p_adjoint)

@@ -36,6 +36,9 @@ class GridSpec:
     n_bg: float = 1.0
     pad_lo: tuple = (0, 0, 0)
     pad_hi: tuple = (0, 0, 0)
+    layer_round_trip: float = 0.0    # absorbing layers as in CBSPlan (0: defaults)
+    layer_power: float = 0.0
+    layer_corner_max: bool = False
 
     @property
     def shape(self):
@@ -130,6 +133,9 @@ class Server:
             r.pad_lo[i] = int(grid.pad_lo[i])
             r.pad_hi[i] = int(grid.pad_hi[i])
             r.r0[i] = int(r0[i])
+        r.layer_round_trip = float(grid.layer_round_trip)
+        r.layer_power = float(grid.layer_power)
+        r.layer_corner_max = 1 if grid.layer_corner_max else 0
         if isinstance(eps, torch.Tensor):
             if eps.dtype != torch.float32 or not eps.is_cuda or not eps.is_contiguous() or tuple(eps.shape) != grid.shape:
                 raise ValueError("eps must be a contiguous float32 CUDA tensor of the grid's shape")
@@ -192,6 +198,13 @@ class Server:
         L.check(self.lib.cbs_server_info(self.handle, ctypes.byref(q), ctypes.byref(a), ctypes.byref(b)))
         return {"queued": q.value, "active": a.value, "bytes_used": b.value}
 
+    def sharing(self):
+        """Launch sharing so far: iteration launches, request iterations they carried, and the
+        most requests one launch carried."""
+        n, m, mx = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_int()
+        L.check(self.lib.cbs_server_sharing(self.handle, ctypes.byref(n), ctypes.byref(m), ctypes.byref(mx)))
+        return {"launches": n.value, "request_iterations": m.value, "max_members": mx.value}
+
 
 # ------------------------------------------------------------------ timed request streams
 @dataclass
@@ -244,44 +257,56 @@ def run_stream(server: Server, requests: Sequence[dict], make_eps, speed: float 
                         len(results) / span if span > 0 else float("nan"), span, peak)
 
 
-def stream_request(rq: dict) -> dict:
+# Absorbing-layer settings of a stream: the defaults, or the gentler one (round trip 1e-2,
+# the largest profile where layers overlap) that converges in about a fifth of the iterations
+LAYERS = {"default": {}, "gentle": {"layer_round_trip": 1e-2, "layer_corner_max": True}}
+
+
+def stream_request(rq: dict, layers: str = "default") -> dict:
     """A request of inputs.serving_stream as the grid / source / r0 this module submits."""
-    g = GridSpec(rq["nx"], rq["ny"], rq["nz"], rq["pitch"], rq["lam"], 1.0, tuple(rq["pads"]), tuple(rq["pads"]))
+    g = GridSpec(rq["nx"], rq["ny"], rq["nz"], rq["pitch"], rq["lam"], 1.0, tuple(rq["pads"]), tuple(rq["pads"]),
+                 **LAYERS[layers])
     return dict(rq, grid=g, source=PlaneWave(pol=rq["pol"]))
 
 
 def measure_stream(requests: int, sizes, ppl: int = 8, load: float = 0.8, max_active: int = 8,
-                   tol: float = 1e-4, seed: int = 42, log=None) -> dict:
-    """Serve a seeded stream (inputs.serving_stream) at `load` times the single-solve service
-    rate and report latency percentiles and throughput, next to the service times of the same
-    request classes solved alone.  log(tag, request, result) sees every result."""
+                   tol: float = 1e-4, seed: int = 42, layers: str = "default", log=None) -> dict:
+    """Serve a seeded stream (inputs.serving_stream, every size equally often) at `load` times
+    the single-solve service rate and report latency percentiles and throughput, next to the
+    service times of the same requests solved alone, one at a time.  log(tag, request, result)
+    sees every result."""
     from . import inputs
-    reqs = [stream_request(rq) for rq in inputs.serving_stream(requests, sizes, seed=seed, ppl=ppl)]
-    alone = {}
+    reqs = [stream_request(rq, layers) for rq in inputs.serving_stream(requests, sizes, seed=seed, ppl=ppl,
+                                                                       balanced=True)]
+    alone = []
     with Server(max_active=1, tol=tol) as srv:
         for rq in reqs:
-            key = (rq["grid"], rq["adjoint"])
-            if key in alone:
-                continue
             srv.submit(rq["grid"], inputs.request_eps(rq), rq["source"], rq["r0"], adjoint=rq["adjoint"])
             r = srv.wait(1)[0]
             if log:
                 log("alone", rq, r)
-            alone[key] = r.t_done - r.t_admit
-    mean_service = float(np.mean([alone[(rq["grid"], rq["adjoint"])] for rq in reqs]))
-    rate = load / mean_service
+            alone.append(r.t_done - r.t_admit)
+    rate = load / float(np.mean(alone))
     inputs.assign_arrivals(reqs, rate, seed=seed)
     with Server(max_active=max_active, tol=tol) as srv:
         rep = run_stream(srv, reqs, inputs.request_eps)
+        sharing = srv.sharing()
     if log:
         for r in rep.results:
             log("stream", reqs[r.tag], r)
-    single = [alone[(rq["grid"], rq["adjoint"])] for rq in reqs]
-    return {"requests": len(reqs), "sizes": [list(v) for v in sizes], "tol": tol, "max_active": max_active,
-            "arrival_rate_hz": rate, "offered_load": load,
+    by_size = {}
+    for rq, r in zip(reqs, sorted(rep.results, key=lambda r: r.tag)):
+        by_size.setdefault("x".join(map(str, (rq["nx"], rq["ny"], rq["nz"]))), []).append(r.latency)
+    return {"requests": len(reqs), "sizes": [list(v) for v in sizes], "tol": tol, "layers": layers,
+            "max_active": max_active, "arrival_rate_hz": rate, "offered_load": load,
             "p50_latency_s": rep.p50_s, "p99_latency_s": rep.p99_s, "mean_latency_s": rep.mean_s,
             "solves_per_s": rep.solves_per_s, "makespan_s": rep.makespan_s, "peak_active": rep.peak_active,
-            "single_solve_p50_s": percentile(single, 50), "single_solve_p99_s": percentile(single, 99),
+            "single_solve_p50_s": percentile(alone, 50), "single_solve_p99_s": percentile(alone, 99),
+            "single_solve_total_s": float(np.sum(alone)),
+            "p50_latency_s_by_size": {k: percentile(v, 50) for k, v in by_size.items()},
+            "requests_by_size": {k: len(v) for k, v in by_size.items()},
+            "launches": sharing["launches"], "request_iterations": sharing["request_iterations"],
+            "max_requests_per_launch": sharing["max_members"],
             "failed": sum(1 for r in rep.results if not r.ok)}
 
 
@@ -301,6 +326,7 @@ def main():
     ap.add_argument("--max-active", type=int, default=8)
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--seed", type=int, default=42)
+    ap.add_argument("--layers", choices=sorted(LAYERS), default="default", help="absorbing-layer setting")
     ap.add_argument("--verbose", action="store_true", help="one line per result on stderr")
     args = ap.parse_args()
 
@@ -313,7 +339,7 @@ def main():
 
     sizes = [inputs.parse_size(v) for v in args.sizes]
     print(json.dumps(measure_stream(args.requests, sizes, args.ppl, args.load, args.max_active, args.tol,
-                                    args.seed, log)))
+                                    args.seed, args.layers, log)))
 
 
 if __name__ == "__main__":

@@ -5,7 +5,11 @@ the GPU forms h_eff in FP32 and the oracle in FP64, so a pixel whose h_eff sits 
 1e-3 voxel of a voxel face may pick the other voxel.  The kernel test feeds the GPU's own
 h_eff to the oracle's chain rule (then only the rounding of h_eff / pitch separates the
 decisions); the full step compares on pixels that no ambiguous pixel can reach through the
-smoothing and the mirror average, at least half of the map.  Adam's first step is alpha * g / (|g| + eps)
+smoothing and the mirror average: at least half of the map with the Gaussian filter, and at
+least 99 % without it (sigma = 0), where a pixel's reach is itself and its mirror images.
+The fill fraction keeps eps continuous in h, so a flipped decision changes only the surface
+derivative of the pixels it reaches, not the field.  Each case prints its ambiguous-pixel
+count.  Adam's first step is alpha * g / (|g| + eps)
 ~ alpha sign(g): where |dL/dh| is below 1e-3 of its maximum the sign is not resolved by an
 FP32 gradient, and there the check is that the step is valid (|dh| <= alpha, within the box).
 """
@@ -52,11 +56,13 @@ def _design(plan, prm):
                   prm.alpha, prm.beta1, prm.beta2, prm.adam_eps)
 
 
-def _trusted_pixels(h_eff_oracle, p_um, prm, tol=1e-3):
+def _trusted_pixels(h_eff_oracle, p_um, prm, tol=1e-3, label=""):
     """Pixels whose dL/dh cannot depend on an ambiguous surface voxel (u within tol of a face
     above the base; u ~ 0 is not ambiguous, h_eff >= 0 on both sides)."""
     u = od.surface_coordinate(h_eff_oracle, p_um)
     amb = (np.abs(u - np.round(u)) < tol) & (np.round(u) >= 1)
+    print(f"{label} sigma={prm.sigma_um} mirror={prm.mirror}: {int(amb.sum())} ambiguous pixels "
+          f"of {amb.size} (tol {tol:g} voxel)")
     R = int(np.ceil(4 * prm.sigma_um / p_um)) if prm.sigma_um > 0 else 0
     reach = np.zeros_like(amb)
     for y, x in zip(*np.nonzero(amb)):
@@ -92,16 +98,18 @@ def test_pipeline_kernels_match_oracle(sigma_um, mirror):
     # voxel) separates the two decisions
     he_gpu = he.cpu().numpy().astype(np.float64)
     gh_ref = od.height_gradient(grad_eps.astype(np.float64), he_gpu, p_um, prm, 1.0)
-    ok = _trusted_pixels(he_gpu, p_um, prm, tol=1e-5)
-    assert ok.mean() >= 0.5
+    ok = _trusted_pixels(he_gpu, p_um, prm, tol=1e-5, label="kernels")
+    assert ok.mean() >= (0.99 if sigma_um == 0 else 0.5)
     err = np.abs(gh.cpu().numpy() - gh_ref)[ok]
     assert np.max(err) <= 1e-5 * np.abs(gh_ref).max()
 
 
-def test_design_step_matches_oracle_at_equal_iterations():
+@pytest.mark.parametrize("sigma_um,mirror,min_trusted", [(0.355, True, 0.5), (0.0, True, 0.99),
+                                                       (0.0, False, 0.99)])
+def test_design_step_matches_oracle_at_equal_iterations(sigma_um, mirror, min_trusted):
     torch = _torch()
     from paper_2506_15411_gb300 import CBSPlan, PlaneWave
-    g, prm, h0, r0 = _case()
+    g, prm, h0, r0 = _case(sigma_um, mirror)
     p_um = g.pitch * 1e6
     K = 300
     st = od.AdamState.zeros(h0.shape)
@@ -116,8 +124,8 @@ def test_design_step_matches_oracle_at_equal_iterations():
             h1, gh1 = h.cpu().numpy(), gh.cpu().numpy()
     assert info.fwd.iters == K and info.adj.iters == K
     assert abs(info.objective - ref.objective) <= 1e-4 * ref.objective
-    ok = _trusted_pixels(ref.h_eff, p_um, prm)
-    assert ok.mean() >= 0.5
+    ok = _trusted_pixels(ref.h_eff, p_um, prm, label="step")
+    assert ok.mean() >= min_trusted, ok.mean()
     gmax = np.abs(ref.grad_h).max()
     assert np.linalg.norm((gh1 - ref.grad_h)[ok]) <= 1e-3 * np.linalg.norm(ref.grad_h[ok])
     mask = od.aperture(g.nx, g.ny, p_um, prm.aperture_um)
@@ -128,7 +136,8 @@ def test_design_step_matches_oracle_at_equal_iterations():
     weak = mask & ~strong
     assert np.all(np.abs(h1[weak] - h0[weak]) <= prm.alpha * (1 + 1e-5))
     assert h1.min() >= 0.0 and h1.max() <= prm.h_max_um
-    assert np.array_equal(h1, h1[::-1, :]) and np.array_equal(h1, h1[:, ::-1])
+    if mirror:
+        assert np.array_equal(h1, h1[::-1, :]) and np.array_equal(h1, h1[:, ::-1])
 
 
 def test_warm_started_steps_converge_to_the_same_result_in_fewer_iterations():

@@ -2,17 +2,21 @@
 
 * every result is bit-for-bit the same alone (one request on the GPU at a time) and in a mix
   of requests of different shapes admitted together;
-* a served solve equals the same solve through a plan (itself checked against the oracle);
+* a served solve equals the same solve through a plan, and a served request of fixed length
+  (tol 0) matches the FP64 oracle element by element: field, adjoint-driven gradient and
+  objective;
 * admission never holds more device memory than the budget, and a request that can never
   fit ends with CBS_ERR_OOM instead of waiting;
 * requests are admitted while others run (no more than max_active at a time) and their work
-  overlaps.
+  overlaps;
+* same-shape requests in flight share the launches of their iterations.
 """
 from __future__ import annotations
 
 import numpy as np
 import pytest
 
+from oracle import cbs_oracle as co
 from paper_2506_15411_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -85,6 +89,32 @@ def test_served_solve_equals_the_plan_path():
     assert torch.equal(r.E, E) and torch.equal(r.grad, grad)
 
 
+def test_served_request_matches_the_oracle_at_fixed_iterations():
+    torch = _torch()
+    from paper_2506_15411_gb300.serve import Server
+    K = 200
+    rq = [q for q in _stream(8) if q["adjoint"] and q["grid"].nx == 32][0]
+    g = rq["grid"]
+    eps = inputs.request_eps(rq)
+    with Server(max_active=2, tol=0.0, max_iter=K, check_every=50) as srv:
+        _submit(srv, rq)
+        r = srv.wait(1)[0]
+    torch.cuda.synchronize()
+    assert r.ok, r.error      # tol 0: exactly K iterations each, no stopping rule applies
+    assert r.fwd.iters == K and r.adj.iters == K
+    og = co.Grid(g.nx, g.ny, g.nz, g.pitch, g.lam, g.n_bg, g.pad_lo, g.pad_hi)
+    fwd = co.forward(og, eps.astype(np.float64), co.plane_wave_source(og, pol=rq["pol"]), tol=0.0, max_iter=K)
+    adj = co.adjoint(og, eps.astype(np.float64), fwd.E, rq["r0"], tol=0.0, max_iter=K)
+    grad = co.gradient(og, fwd.E, adj.E)
+    obj = co.objective(fwd.E, rq["r0"])
+    E = r.E.cpu().numpy()
+    assert np.linalg.norm(E - fwd.E) <= 2e-5 * np.linalg.norm(fwd.E)
+    gg = r.grad.cpu().numpy()
+    assert np.linalg.norm(gg - grad) <= 1e-4 * np.linalg.norm(grad)
+    assert abs(r.objective - obj) <= 1e-5 * obj
+    assert abs(r.fwd.rel_resid - fwd.rel_resid) <= 1e-3 * fwd.rel_resid
+
+
 def test_admission_stays_within_the_memory_budget():
     torch = _torch()
     from paper_2506_15411_gb300._lib import CBS_ERR_OOM
@@ -144,9 +174,9 @@ def test_a_large_request_is_not_starved_by_a_stream_of_small_ones():
     small = GridSpec(32, 32, 32, lam / 8, lam, 1.0, (4, 4, 4), (4, 4, 4))
     large = GridSpec(64, 64, 64, lam / 8, lam, 1.0, (8, 8, 8), (8, 8, 8))
 
-    def slot_bytes(g):   # the server's footprint of a slot: plan (planes of up to ny + 1
-        nxp = (g.nx + 15) // 16 * 16   # padded rows), eps, E, E_adj, gradient
-        return nxp * (g.ny + 1) * g.nz * 56 + g.nx * g.ny * g.nz * 56 + (16 << 20)
+    def slot_bytes(g):   # the server's footprint of a one-seat batch: the plan's arrays at
+        nxp = (g.nx + 15) // 16 * 16   # padded rows, eps, E, E_adj, gradient, 16 MB of tables
+        return nxp * g.ny * g.nz * 56 + g.nx * g.ny * g.nz * 56 + (16 << 20)
 
     budget = (slot_bytes(large) + (1 << 20)) / 1e9
     eps_s = inputs.random_eps(32, 32, 32, seed=21)
@@ -164,3 +194,37 @@ def test_a_large_request_is_not_starved_by_a_stream_of_small_ones():
     passed = sum(1 for i in range(2, 26) if res[("s", i)].t_admit < big.t_admit)
     assert passed <= 8, passed
     assert big.fwd.iters > 0
+
+
+def test_same_shape_requests_share_launches():
+    """Four same-shape requests admitted together run in one batch: launches carry several of
+    them, and each result equals the one it gets alone."""
+    torch = _torch()
+    from paper_2506_15411_gb300.serve import Server
+    reqs = [q for q in _stream(24, seed=11) if q["grid"].nx == 32][:4]
+    assert len(reqs) == 4
+    alone = {}
+    with Server(max_active=1, tol=1e-4, check_every=16) as srv:
+        for rq in reqs:
+            _submit(srv, rq)
+            r = srv.wait(1)[0]
+            alone[r.tag] = r
+        sh1 = srv.sharing()
+    with Server(max_active=4, tol=1e-4, check_every=16) as srv:
+        for rq in reqs:
+            _submit(srv, rq)
+        mix = {r.tag: r for r in srv.wait(len(reqs))}
+        sh = srv.sharing()
+    torch.cuda.synchronize()
+    assert sh1["max_members"] == 1 and sh1["request_iterations"] == sh1["launches"]
+    assert sh["max_members"] >= 2, sh
+    total = sum(r.fwd.iters + r.adj.iters for r in mix.values())
+    assert sh["request_iterations"] == total, (sh, total)
+    assert sh["launches"] < sh["request_iterations"], sh
+    for rq in reqs:
+        a, b = alone[rq["index"]], mix[rq["index"]]
+        assert a.ok and b.ok, (a.error, b.error)
+        assert a.fwd.iters == b.fwd.iters and a.adj.iters == b.adj.iters
+        assert torch.equal(a.E, b.E)
+        if rq["adjoint"]:
+            assert torch.equal(a.grad, b.grad)
