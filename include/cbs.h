@@ -292,7 +292,8 @@ int cbs_design_step(cbs_design_t design, float* h_dev, const cbs_source* src, co
  * every batch one block of check_every iterations at a time without waiting on any one of
  * them; each launch of a block carries every iterating request of the batch (the kernels'
  * tile space has a request index), so same-shape requests in flight share the launches, and
- * batches of different shapes run side by side on their own streams.  A request arriving
+ * batches of different shapes run side by side on their own streams, smaller grids at higher
+ * stream priority (a short request's next kernel goes before a long one's).  A request arriving
  * while others run takes a free seat at the next block, or a new batch when memory allows;
  * a batch is created with as many seats as the budget leaves room for.  Batches without
  * requests are kept for later requests of their shape and evicted, least recently used

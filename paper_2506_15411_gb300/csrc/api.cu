@@ -125,14 +125,6 @@ bool encode_w_map(CUtensorMap* tm, float2* W, int nx, int ny, int nz, int nxp, i
 
 
 
-bool same_source(const SourceArgs& a, const SourceArgs& b) {
-  if (a.kind != b.kind || a.zp != b.zp || a.px != b.px || a.py != b.py || a.pz != b.pz ||
-      a.amp_dev != b.amp_dev || a.user != b.user || a.user_scale != b.user_scale)
-    return false;
-  for (int c = 0; c < 3; ++c)
-    if (a.amp[c].x != b.amp[c].x || a.amp[c].y != b.amp[c].y) return false;
-  return true;
-}
 
 }  // namespace
 
@@ -219,7 +211,7 @@ int graph_block(cbs_plan_s* p, const IterArgs& a, int n, bool& used) {
   used = false;
   cudaGraphExec_t exec = nullptr;
   for (auto& g : p->graphs)
-    if (g.E == a.E && g.iters == n && same_source(g.src, a.mem[0].src)) exec = g.exec;
+    if (g.E == a.E && g.iters == n) exec = g.exec;
   if (!exec) {
     if (p->graphs.size() >= 8) drop_graphs(p);
     cudaGraph_t g = nullptr;
@@ -237,7 +229,7 @@ int graph_block(cbs_plan_s* p, const IterArgs& a, int n, bool& used) {
     e = cudaGraphInstantiate(&ex, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(CBS_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
-    p->graphs.push_back(GraphEntry{a.E, a.mem[0].src, n, ex});
+    p->graphs.push_back(GraphEntry{a.E, n, ex});
     exec = ex;
   }
   CK(cudaGraphLaunch(exec, p->stream));
@@ -387,12 +379,19 @@ void series_begin(cbs_plan_s* p, float2* E, const SourceArgs& src, int warm, Ser
   }
   R.a = p->base;
   R.a.E = p->Ei;   // iterate on the plan's padded copy; the caller's E is read and written once
-  R.a.nmem = 1;    // the plan's own solves use seat 0
-  R.a.mem[0].src = src;
+  R.a.nmem = 1;    // the plan's own solves use seat 0 and member 0
+  R.a.mem = p->mem_dev;
+  Member& m = p->mem_host[0];   // (the previous solve's copy of it has completed)
+  m = Member{};
+  m.src = src;
+  m.inv_eps = (float)(1.0 / p->eps_s);
+  m.kt2 = make_float2((float)p->k0sq_s, (float)p->eps_s);
+  m.seat = 0;
   // every run starts from a clean error flag and residual counter: a run that a timed-out
   // tensor-copy wait ended left both behind, and everything else it touched (W, the
   // iterate, the partial sums) is recomputed from the plan's inputs below
-  cudaError_t e = cudaMemsetAsync(p->Ei, 0, 3 * R.a.Nw * sizeof(float2), p->stream);
+  cudaError_t e = cudaMemcpyAsync(p->mem_dev, p->mem_host, sizeof(Member), cudaMemcpyHostToDevice, p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->Ei, 0, 3 * R.a.Nw * sizeof(float2), p->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->counter, 0, sizeof(unsigned), p->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->err_dev, 0, sizeof(int), p->stream);
   if (e != cudaSuccess) {
@@ -585,9 +584,12 @@ int plan_create(cbs_plan_s** out, const cbs_plan_desc* desc, int seats) {
   if (!layer_spec_valid(layers))
     return fail(CBS_ERR_ARG, "layer round trip %g, power %g or corner rule %d out of range", d.layer_round_trip,
                 d.layer_power, d.layer_corner_max);
+  // radices up to 11 where the axis allows (kernels built for them need fewer registers, and
+  // the y pass then runs two blocks per SM: 256 = 8 8 4 beat 16 16 by 18 % per iteration on a
+  // 256 x 256 x 192 grid), else up to 16 (axes with a factor 13)
   std::vector<int> rad[3];
   for (int a2 = 0; a2 < 3; ++a2)
-    if (!factor_radices(dims[a2], 16, rad[a2]))
+    if (!factor_radices(dims[a2], 11, rad[a2]) && !factor_radices(dims[a2], 16, rad[a2]))
       return fail(CBS_ERR_ARG, "axis %d size %d is not a product of 2,3,5,7,11,13", a2, dims[a2]);
 
   cbs_plan_s* p = new cbs_plan_s();
@@ -743,6 +745,8 @@ int plan_create(cbs_plan_s** out, const cbs_plan_desc* desc, int seats) {
   CKP(cudaMemset(p->counter, 0, S * sizeof(unsigned)));
   CKP(cudaMalloc(&p->hist, S * d.check_every * sizeof(double)));
   CKP(cudaMallocHost(&p->hist_host, S * d.check_every * sizeof(double)));
+  CKP(cudaMalloc(&p->mem_dev, members_len(seats, d.check_every) * sizeof(Member)));
+  CKP(cudaMallocHost(&p->mem_host, members_len(seats, d.check_every) * sizeof(Member)));
   CKP(cudaMalloc(&p->adj_amp, S * 3 * sizeof(float2)));
   CKP(cudaMalloc(&p->dobj, S * sizeof(double)));
   p->seat_k0sq.assign(seats, 0.0);
@@ -838,7 +842,7 @@ int plan_create(cbs_plan_s** out, const cbs_plan_desc* desc, int seats) {
   a.E = p->Ei;
   a.seats = seats;
   a.nmem = 1;
-  a.mem[0] = Member{};
+  a.mem = p->mem_dev;
   a.err = p->err_dev;
   a.partials = p->partials;
   a.counter = p->counter;
@@ -864,12 +868,14 @@ void cbs_destroy(cbs_plan_t p) {
   cudaSetDevice(p->device);
   if (p->stream) cudaStreamSynchronize(p->stream);
   drop_graphs(p);
-  void* devs[] = {p->V, p->W, p->Ei, p->tw, p->pq, p->stages, p->partials, p->counter, p->hist, p->adj_amp, p->dobj,
+  void* devs[] = {p->V, p->W, p->Ei, p->tw, p->pq, p->stages, p->partials, p->counter, p->hist, p->mem_dev,
+                  p->adj_amp, p->dobj,
                   p->sx, p->sy, p->sz, p->pmin, p->pmax, p->pbad, p->pdev, p->eps_dev,
                   p->Ef, p->Ea, p->grad_dev, p->err_dev};
   for (void* q : devs)
     if (q) cudaFree(q);
   if (p->hist_host) cudaFreeHost(p->hist_host);
+  if (p->mem_host) cudaFreeHost(p->mem_host);
   if (p->err_host) cudaFreeHost(p->err_host);
   if (p->ev) cudaEventDestroy(p->ev);
   if (p->blk_ev) cudaEventDestroy(p->blk_ev);
@@ -917,19 +923,30 @@ int cbs_set_solver(cbs_plan_t p, double tol, int max_iter, int check_every) {
     drop_graphs(p);
     double* h = nullptr;
     double* hh = nullptr;
-    const size_t n = (size_t)p->seats * check_every;
-    CK(cudaMalloc(&h, n * sizeof(double)));
-    cudaError_t e = cudaMallocHost(&hh, n * sizeof(double));
+    Member* md = nullptr;
+    Member* mh = nullptr;
+    const size_t n = (size_t)p->seats * check_every, nm = members_len(p->seats, check_every);
+    cudaError_t e = cudaMalloc(&h, n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&hh, n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&md, nm * sizeof(Member));
+    if (e == cudaSuccess) e = cudaMallocHost(&mh, nm * sizeof(Member));
     if (e != cudaSuccess) {
-      cudaFree(h);
-      return fail(CBS_ERR_CUDA, "cudaMallocHost: %s", cudaGetErrorString(e));
+      if (h) cudaFree(h);
+      if (hh) cudaFreeHost(hh);
+      if (md) cudaFree(md);
+      return fail(CBS_ERR_CUDA, "solver buffers: %s", cudaGetErrorString(e));
     }
     cudaFree(p->hist);
     cudaFreeHost(p->hist_host);
+    cudaFree(p->mem_dev);
+    cudaFreeHost(p->mem_host);
     p->hist = h;
     p->hist_host = hh;
+    p->mem_dev = md;
+    p->mem_host = mh;
     p->base.hist = h;
     p->base.hist_cap = check_every;
+    p->base.mem = md;
   }
   p->d.tol = tol;
   p->d.max_iter = max_iter;
@@ -954,11 +971,7 @@ int cbs_set_permittivity(cbs_plan_t p, const float* eps) {
   if (rc) return rc;
   p->k0sq_s = p->seat_k0sq[0];
   p->eps_s = p->seat_eps[0];
-  Member& m = p->base.mem[0];
-  m.inv_eps = (float)(1.0 / p->eps_s);
-  m.kt2 = make_float2((float)p->k0sq_s, (float)p->eps_s);
-  p->have_eps = true;
-  drop_graphs(p);   // kernel parameters changed
+  p->have_eps = true;   // (the splitting reaches the kernels through the member array)
   return CBS_OK;
 }
 

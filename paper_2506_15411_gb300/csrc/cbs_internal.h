@@ -23,9 +23,10 @@ struct SourceArgs {
 
 // Requests that share one launch: a plan's arrays (E, W, V) hold `seats` requests of the same
 // grid side by side, and a launch iterates up to kMaxMembers of them, each with its own source
-// and splitting.  A launch's grid is nmem times the per-request persistent grid; block b works
-// for member b / grid, as block b mod grid of that request's own persistent grid, so every
-// request's tiles, and the order of its residual sums, are the same in any launch.
+// and splitting (an array of Member in device memory, written before the launch).  A launch's
+// grid is nmem times the per-request persistent grid; block b works for member b / grid, as
+// block b mod grid of that request's own persistent grid, so every request's tiles, and the
+// order of its residual sums, are the same in any launch.
 constexpr int kMaxMembers = 8;
 
 struct Member {
@@ -58,7 +59,7 @@ struct IterArgs {
   const float2* V;        // potential [seats][nyb][nz][yblk][nxp], scaled
   int seats;              // requests the arrays hold
   int nmem;               // members of this launch (1 .. kMaxMembers)
-  Member mem[kMaxMembers];
+  const Member* mem;      // their sources, splittings and seats (device memory)
   float invN;             // 1 / N, folded into the k-space multiply
   double* partials;       // residual partial sums, [seat][grid_x]
   unsigned* counter;      // last-block-done counters, [seat] (left at 0)

@@ -42,13 +42,19 @@ inline bool nonfatal(int rc) {
   return rc == CBS_OK || rc == CBS_ERR_NOT_CONVERGED || rc == CBS_ERR_STAGNATED || rc == CBS_ERR_TIME_LIMIT;
 }
 
-// A captured block of iterations bakes in the field pointer and the whole source.
+// A captured block of iterations (the launches read the source and splitting from the plan's
+// member array, so a graph serves every solve of the plan).
 struct GraphEntry {
   float2* E;
-  SourceArgs src;
   int iters;
   cudaGraphExec_t exec;
 };
+
+// Length of a plan's member array: [0] the plan's own solves, [1 + s] seat s alone (a series'
+// first x pass), then check_every lists of kMaxMembers for a batch's block of iterations.
+inline size_t members_len(int seats, int check_every) {
+  return 1 + (size_t)seats + (size_t)check_every * kMaxMembers;
+}
 
 }  // namespace cbs
 
@@ -80,6 +86,8 @@ struct cbs_plan_s {
   double* partials = nullptr;
   unsigned* counter = nullptr;
   double* hist = nullptr;
+  cbs::Member* mem_dev = nullptr;   // launch members (members_len) and their pinned staging
+  cbs::Member* mem_host = nullptr;
   float2* adj_amp = nullptr;
   double* dobj = nullptr;
   double *sx = nullptr, *sy = nullptr, *sz = nullptr;

@@ -16,7 +16,7 @@
 // A request's result is the same alone and in any mix: its blocks of a launch are the blocks
 // of its own persistent grid (so its tiles and the order of its residual sums do not depend
 // on the other members), seats share no device memory, and the stopping decision depends on
-// the request's own residuals only.
+// the request's own residuals only.  Batches of smaller grids run on higher-priority streams.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -180,14 +180,27 @@ void finish(cbs_server_s* S, Batch* b, Seat& s, int status) {
   b->last_used = now_s();
 }
 
+// Stream priority of a batch: smaller grids get higher priority (one level per factor of 4 in
+// voxels above 2^20, as far as the device's range goes), so that when batches of different
+// sizes are in flight the GPU picks a small request's next kernel before a large one's and
+// short requests are not held to the pace of long ones.
+int batch_priority(size_t voxels) {
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return 0;
+  int level = 0;
+  for (size_t v = (size_t)1 << 21; v < voxels && greatest + level < least; v <<= 2) ++level;
+  return greatest + level;
+}
+
 int make_batch(cbs_server_s* S, const ShapeKey& k, int seats, Batch** out) {
   auto* b = new Batch;
   b->key = k;
   b->bytes = batch_bytes(k, seats);
   b->seats.resize(seats);
   const size_t N = (size_t)k.nx * k.ny * k.nz;
-  cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->setup, cudaStreamNonBlocking);
+  const int prio = batch_priority(N);
+  cudaError_t e = cudaStreamCreateWithPriority(&b->stream, cudaStreamNonBlocking, prio);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b->setup, cudaStreamNonBlocking, prio);
   for (int i = 0; i < seats && e == cudaSuccess; ++i) {
     Seat& s = b->seats[i];
     s.idx = i;
@@ -244,9 +257,13 @@ int seat_begin(Batch* b, Seat& s, float2* E, const SourceArgs& src, Phase phase)
   const size_t Nw = p->base.Nw;
   CK(cudaMemsetAsync(p->Ei + (size_t)s.idx * 3 * Nw, 0, 3 * Nw * sizeof(float2), b->stream));
   CK(cudaMemsetAsync(p->counter + s.idx, 0, sizeof(unsigned), b->stream));
+  // the seat's own member slot (its previous copy completed with its previous series)
+  p->mem_host[1 + s.idx] = s.mem;
+  CK(cudaMemcpyAsync(p->mem_dev + 1 + s.idx, p->mem_host + 1 + s.idx, sizeof(Member), cudaMemcpyHostToDevice,
+                     b->stream));
   IterArgs a = p->base;
   a.nmem = 1;
-  a.mem[0] = s.mem;
+  a.mem = p->mem_dev + 1 + s.idx;
   CK(launch_xpass_fwd(a, b->stream));
   s.phase = phase;
   return CBS_OK;
@@ -310,11 +327,22 @@ int enqueue_block(cbs_server_s* S, Batch* b) {
     L = std::max(L, s.blk);
   }
   if (L == 0) return CBS_OK;
+  // the member lists of the block's iterations, staged and copied at once (the previous
+  // block's copy has completed: its event was waited for)
+  const size_t base = 1 + (size_t)p->seats;
+  std::vector<int> nm(L);
+  for (int k = 0; k < L; ++k) {
+    Member* list = p->mem_host + base + (size_t)k * kMaxMembers;
+    nm[k] = 0;
+    for (const Seat& s : b->seats)
+      if (s.blk > k) list[nm[k]++] = s.mem;
+  }
+  CK(cudaMemcpyAsync(p->mem_dev + base, p->mem_host + base, (size_t)L * kMaxMembers * sizeof(Member),
+                     cudaMemcpyHostToDevice, b->stream));
   IterArgs a = p->base;
   for (int k = 0; k < L; ++k) {
-    a.nmem = 0;
-    for (const Seat& s : b->seats)
-      if (s.blk > k) a.mem[a.nmem++] = s.mem;
+    a.nmem = nm[k];
+    a.mem = p->mem_dev + base + (size_t)k * kMaxMembers;
     a.slot = k;
     const int rc = launch_iteration(p, a, b->stream, nullptr);
     if (rc) return rc;

@@ -29,8 +29,7 @@ namespace cbs {
 namespace {
 
 // The source of component c at voxel (x, y, z); kind and plane (the sheet's z, or the point's
-// z) are s.kind and s.zp / s.pz, read once into registers by the caller (s itself sits in the
-// launch's parameters at a member index known only at run time).
+// z) are s.kind and s.zp / s.pz, read once into registers by the caller.
 __device__ __forceinline__ float2 source_at(const IterArgs& a, const SourceArgs& s, int kind, int plane, int c,
                                             int z, int y, int x) {
   if (kind == 0) {
@@ -173,7 +172,7 @@ __device__ __forceinline__ void row_stages(float2* buf, int cs, int ld, int nr, 
 // Persistent forward x pass (a series' first iteration): V E + S formed as the first stage
 // loads each element, transformed in place in the E buffer, stored as W.
 template <int MAXR>
-__global__ void __launch_bounds__(kThreads, kXOcc) k_xpass_fwd(const __grid_constant__ IterArgs a) {
+__global__ void __launch_bounds__(kThreads, kXOcc) k_xpass_fwd(const IterArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int rpb = a.rpb, nxp = a.nxp, nset = a.nset_xf;
   const int span = rpb * nxp;
@@ -259,7 +258,7 @@ __global__ void __launch_bounds__(kThreads, kXOcc) k_xpass_fwd(const __grid_cons
 // A group whose copy wait times out records the error and stops taking tiles, but still
 // joins the block's final residual reduction.
 template <int MAXR>
-__global__ void __launch_bounds__(kThreads, kXOcc) k_xpass_inv_fwd(const __grid_constant__ IterArgs a) {
+__global__ void __launch_bounds__(kThreads, kXOcc) k_xpass_inv_fwd(const IterArgs a) {
   const int NG = a.xgroups, GT = kThreads / NG;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int rpb = a.rpb, nxp = a.nxp, nset = a.nset_x;

@@ -113,7 +113,7 @@ __device__ __forceinline__ void col_stages(float2* buf, int cs, const AxisIP& ap
 // the other waits at a barrier).
 template <int TX, bool INV, int OCC>
 __global__ void __launch_bounds__(y_threads<OCC>(), OCC) k_ypass(const __grid_constant__ CUtensorMap tm,
-                                                                const __grid_constant__ IterArgs a) {
+                                                                const IterArgs a) {
   constexpr int MAXR = OCC == 1 ? 16 : 11;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int tileN = a.nyr * TX, nbuf = a.nbuf_y;
@@ -187,7 +187,7 @@ __device__ __forceinline__ void group_sync(int id, int count) {
 // wave-number tables have their own barrier.
 template <int TX, int MAXR>
 __global__ void __launch_bounds__(kZThreads, kZOcc) k_zpass_green(const __grid_constant__ CUtensorMap tm,
-                                                               const __grid_constant__ IterArgs a) {
+                                                               const IterArgs a) {
   static_assert(kZThreads % (2 * TX) == 0, "a warp group's threads must be a multiple of the tile width");
   const int NG = a.zgroups, GT = kZThreads / NG;
   extern __shared__ __align__(128) unsigned char smem_raw[];

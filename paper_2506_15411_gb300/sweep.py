@@ -7,9 +7,10 @@ next length the FFTs support (prime factors 2, 3, 5, 7, 11, 13), the extra voxel
 background interior.  One JSON line per pitch: grid, voxels, forward iterations to the
 relative residual --tol, seconds (host wall time of the solve, permittivity set-up excluded),
 time per iteration and voxel-iterations per second; a last line fits t = c N^a over the
-sweep.
+sweep.  --layers gentle uses the gentler absorbing layers (round trip 1e-2, the largest
+profile where layers overlap) instead of the defaults.
 
-    python -m paper_2506_15411_gb300.sweep --ppl 6 8 10 12 14 16 18
+    python -m paper_2506_15411_gb300.sweep --ppl 6 8 10 12 14 16 18 [--layers gentle]
 """
 from __future__ import annotations
 
@@ -55,19 +56,22 @@ def main():
     ap.add_argument("--ppl", type=int, nargs="+", default=[6, 8, 10, 12, 14, 16, 18])
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--check-every", type=int, default=64)
+    ap.add_argument("--layers", choices=["default", "gentle"], default="default")
     args = ap.parse_args()
+    layers = {"layer_round_trip": 1e-2, "layer_corner_max": True} if args.layers == "gentle" else {}
     rows = []
     for ppl in args.ppl:
         nx, ny, nz, pitch, pads = grid_for(ppl)
         wl = inputs.fresnel_lens_workload(nx, ny, nz, pitch, LAM, D_UM * 1e-6, NA, N_LENS, pad_lo=pads, pad_hi=pads)
         with CBSPlan(nx, ny, nz, pitch, LAM, 1.0, pads, pads, tol=args.tol, max_iter=200000,
-                     check_every=args.check_every) as plan:
+                     check_every=args.check_every, **layers) as plan:
             plan.set_permittivity(torch.from_numpy(wl.eps).to(plan.device))
             E, st = plan.forward(PlaneWave())          # warm-up of graphs and clocks
             E, st = plan.forward(PlaneWave(), E=E)
             torch.cuda.synchronize()
         N = nx * ny * nz
-        row = {"ppl": ppl, "pitch_nm": pitch * 1e9, "grid": [nx, ny, nz], "voxels": N, "iters": st.iters,
+        row = {"ppl": ppl, "layers": args.layers, "pitch_nm": pitch * 1e9, "grid": [nx, ny, nz], "voxels": N,
+               "iters": st.iters,
                "status": st.status, "seconds": st.seconds, "ms_per_iter": 1e3 * st.seconds / st.iters,
                "voxel_iters_per_s": N * st.iters / st.seconds}
         rows.append(row)
