@@ -201,10 +201,9 @@ int cbs_pass_times(cbs_plan_t plan, double ms_total[5], long long launches[5], i
  *         kernels run on cuda_stream; NULL is the legacy stream); the solver fields are not.
  *   eps_real_dev: float32 [nz][ny][nx] on the current device, layers included.
  * Scratch: one ~80 KB array in device memory per device that loads the library, kept until
- * the process exits.  The first call on a device looks up its address (do that first call
- * before any stream capture) and keeps it for the life of the process: after a
- * cudaDeviceReset of that device the kept address is stale, so do not call this entry point
- * again on a device that has been reset.  Every call shares the array and leaves its contents behind;
+ * the process exits.  The first call on a device looks up its address and keeps it for the
+ * life of the process: after a cudaDeviceReset of that device the kept address is stale, so
+ * do not call this entry point again on a device that has been reset.  Every call shares the array and leaves its contents behind;
  * calls that overlap on the GPU (other streams or threads) race and give wrong results.
  * Limit: nx * ny * nz <= 268,435,456 voxels (4096 blocks of 65,536); larger grids return
  * CBS_ERR_ARG.  Other errors: CBS_ERR_ARG (NULL; dims or pads that cbs_plan rejects:
