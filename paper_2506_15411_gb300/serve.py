@@ -1,12 +1,13 @@
 """Serving: continuous batching of CBS solves over mixed grid sizes.
 
 The server itself is native (cbs_server_* in include/cbs.h): a worker thread admits queued
-requests into per-shape slots within a device-memory budget and advances every admitted
-solve one block of iterations at a time, so new requests start while others run and their
-work interleaves on the GPU.  This module marshals requests and results, and drives a
-stream of timed arrivals for latency measurements:
+requests into per-shape batches within a device-memory budget -- a batch iterates all of its
+requests in the same launches -- and advances every batch one block of iterations at a time,
+so new requests start while others run and batches of different shapes share the GPU.  This
+module marshals requests and results, and drives a stream of timed arrivals for latency
+measurements:
 
-    python -m paper_2506_15411_gb300.serve --requests 40 --sizes 64 128 192x192x128
+    python -m paper_2506_15411_gb300.serve --requests 40 --sizes 64 128 192x192x128 --layers gentle
 
 prints one JSON line: p50 / p99 latency, solves/s, and the single-solve times of the same
 requests run alone.
