@@ -64,6 +64,10 @@ constexpr double kPiD = 3.14159265358979323846;
 constexpr int kMaxYZOcc = CBS_MAX_YZ_OCC;    // a build with 1 keeps every y/z kernel at one block per SM
 constexpr int kMinOcc2Tx = CBS_MIN_OCC2_TX;  // narrowest tile worth two blocks per SM
 constexpr int kYZMaxBuf = CBS_YZ_MAX_BUF;    // most tile buffers of a y or z block
+#ifndef CBS_Z_THREADS
+#define CBS_Z_THREADS 512
+#endif
+constexpr int kZThreadsPlan = CBS_Z_THREADS;  // threads of a z block (as the kernel is built)
 #ifndef CBS_YBLOCK
 #define CBS_YBLOCK 128
 #endif
@@ -772,7 +776,8 @@ int plan_create(cbs_plan_s** out, const cbs_plan_desc* desc, int seats) {
     int twoff[3], pqoff[3];
     for (int a2 = 0; a2 < 3; ++a2) {
       const int n = dims[a2];
-      p->radix_order[a2] = order_radices(rad[a2], n, lay[a2], ncol[a2]);
+      p->radix_order[a2] = a2 == 2 ? order_radices_z(rad[a2], n, a.tx_z, kZThreadsPlan / a.zgroups)
+                                   : order_radices(rad[a2], n, lay[a2], ncol[a2]);
       std::vector<int4> st;
       std::vector<float2> tw, pq;
       axis_tables(n, p->radix_order[a2], st, tw, pq);

@@ -149,6 +149,47 @@ inline std::vector<int> order_radices(const std::vector<int>& radices, int n, Ax
   return best;
 }
 
+// Modelled work of the stages of one z tile for a radix order: per stage, the rounds a warp
+// group of nth threads makes over the stage's items, times the values an item holds.  The
+// stages before the last take column pairs of each of the three components (and run twice:
+// forward and inverse); the last, fused stage takes single columns with all three
+// components and runs its forward and inverse butterflies in one item.  A stage whose items
+// leave most threads idle in its last round costs a whole round.
+inline long long z_balance_cost(const std::vector<int>& order, int n, int ncol, int nth) {
+  long long cost = 0;
+  const int s = (int)order.size();
+  for (int q = 0; q < s; ++q) {
+    const int R = order[q];
+    if (q < s - 1) {
+      const long long items = 3LL * (ncol / 2) * (n / R);
+      cost += 2 * ((items + nth - 1) / nth) * 2 * R;
+    } else {
+      const long long items = (long long)ncol * (n / R);
+      cost += ((items + nth - 1) / nth) * 6 * R;
+    }
+  }
+  return cost;
+}
+
+// The order of the z axis' radices: the least modelled work (z_balance_cost), then the fewest
+// modelled shared-memory wavefronts (layout_cost), then the largest-first order.
+inline std::vector<int> order_radices_z(const std::vector<int>& radices, int n, int ncol, int nth) {
+  std::vector<int> perm = radices;
+  std::sort(perm.begin(), perm.end());
+  std::vector<int> best = radices;
+  long long bw = z_balance_cost(radices, n, ncol, nth), bc = layout_cost(radices, n, AxisLayout::ColsZ, ncol);
+  do {
+    const long long w = z_balance_cost(perm, n, ncol, nth);
+    const long long c = layout_cost(perm, n, AxisLayout::ColsZ, ncol);
+    if (w < bw || (w == bw && c < bc)) {
+      bw = w;
+      bc = c;
+      best = perm;
+    }
+  } while (std::next_permutation(perm.begin(), perm.end()));
+  return best;
+}
+
 // Device tables of an axis for a given radix order (see fft_ip.cuh): the stage table
 // (2 int4 per stage), the twiddle table (complex64, w_n^{j k P_q} at tw_off_q + (k-1) m_q + j,
 // computed in FP64 and rounded), and the wave numbers (p, q) of each position (scaled by the

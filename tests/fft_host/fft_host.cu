@@ -110,6 +110,16 @@ int fh_order(int n, int layout, int ncol, int* order) {
   return (int)A.order.size();
 }
 
+// The z axis' order as the library picks it (radices up to 11 where the axis allows, then
+// the least modelled work for nth threads on ncol-column tiles).
+int fh_order_z(int n, int ncol, int nth, int* order) {
+  std::vector<int> rad;
+  if (!factor_radices(n, 11, rad) && !factor_radices(n, 16, rad)) return -1;
+  const std::vector<int> o = order_radices_z(rad, n, ncol, nth);
+  for (size_t i = 0; i < o.size(); ++i) order[i] = o[i];
+  return (int)o.size();
+}
+
 // Wave numbers (p, q) per position (float2 [n]).
 int fh_pq(int n, int layout, int ncol, float* pq) {
   Axis A;

@@ -111,3 +111,15 @@ def test_radix_order_avoids_modelled_bank_conflicts(fh):
     s = fh.fh_order(336, 2, 8, o)
     assert sorted(o[:s]) == [6, 7, 8]
     assert fh.fh_order(17, 0, 0, o) == -1          # not a product of the supported radices
+
+
+def test_z_radix_order_balances_the_warp_groups_rounds(fh):
+    """The z order puts the radix whose fused-stage items fill the 256-thread warp group best
+    last: 315 = 5 7 9 would run the fused radix-9 stage in two rounds of 280 items (the second
+    nearly idle), 5 9 7 in two rounds of 360; 336 keeps 8 6 7."""
+    o = (ctypes.c_int * 8)()
+    s = fh.fh_order_z(315, 8, 256, o)
+    assert s == 3 and sorted(o[:s]) == [5, 7, 9] and o[s - 1] != 9
+    s = fh.fh_order_z(336, 8, 256, o)
+    assert list(o[:s]) == [8, 6, 7]
+    assert fh.fh_order_z(17, 8, 256, o) == -1
