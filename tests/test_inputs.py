@@ -89,3 +89,18 @@ def test_serving_stream_is_seeded_and_poisson():
     small = inputs.serving_stream(4, sizes=((32, 32, 32),), seed=1)
     e = inputs.request_eps(small[0])
     assert e.shape == (32, 32, 32) and e.dtype == np.float32 and 1.0 <= e.min() and e.max() <= 1.6 ** 2 + 1e-6
+
+
+def test_balanced_serving_stream_covers_every_size_equally():
+    """The measured streams draw every size n // len(sizes) times (or once more), so a short
+    stream still covers all five; the draw is seeded."""
+    for n in (20, 23):
+        a = inputs.serving_stream(n, seed=42, balanced=True)
+        b = inputs.serving_stream(n, seed=42, balanced=True)
+        assert [(q["nx"], q["nz"], q["structure"], q["adjoint"]) for q in a] == \
+               [(q["nx"], q["nz"], q["structure"], q["adjoint"]) for q in b]
+        counts = {s: sum(1 for q in a if (q["nx"], q["ny"], q["nz"]) == s) for s in inputs.SERVING_SIZES}
+        assert set(counts.values()) <= {n // 5, n // 5 + 1} and sum(counts.values()) == n
+    # the order is random, not the sizes in turn
+    a = inputs.serving_stream(20, seed=42, balanced=True)
+    assert [q["nx"] for q in a[:5]] != [s[0] for s in inputs.SERVING_SIZES]
