@@ -228,3 +228,36 @@ def test_same_shape_requests_share_launches():
         assert torch.equal(a.E, b.E)
         if rq["adjoint"]:
             assert torch.equal(a.grad, b.grad)
+
+
+def test_requests_share_launches_only_with_the_same_plan_settings():
+    """Same grid, different absorbing layers: separate batches (a launch never mixes plans);
+    the same layers: one batch.  Each result equals the plan path with its own layers."""
+    torch = _torch()
+    import dataclasses
+    from paper_2506_15411_gb300 import CBSPlan
+    from paper_2506_15411_gb300.serve import Server
+    rq = [q for q in _stream(24, seed=11) if q["grid"].nx == 32][0]
+    g0 = rq["grid"]
+    g1 = dataclasses.replace(g0, layer_round_trip=1e-2, layer_corner_max=True)
+    eps = inputs.request_eps(rq)
+    res = {}
+    for tag, grids in (("mixed", (g0, g1)), ("same", (g1, g1))):
+        with Server(max_active=2, tol=1e-4, check_every=16) as srv:
+            for i, g in enumerate(grids):
+                srv.submit(g, eps, rq["source"], rq["r0"], want_field=True, tag=i)
+            out = {r.tag: r for r in srv.wait(2)}
+            res[tag] = (out, srv.sharing())
+    torch.cuda.synchronize()
+    assert res["mixed"][1]["max_members"] == 1
+    assert res["same"][1]["max_members"] == 2
+    for g, r in ((g0, res["mixed"][0][0]), (g1, res["mixed"][0][1]), (g1, res["same"][0][0])):
+        assert r.ok, r.error
+        with CBSPlan(g.nx, g.ny, g.nz, g.pitch, g.lam, g.n_bg, g.pad_lo, g.pad_hi, tol=1e-4, check_every=16,
+                     layer_round_trip=g.layer_round_trip, layer_corner_max=g.layer_corner_max) as plan:
+            plan.set_permittivity(torch.from_numpy(eps).cuda())
+            E, st = plan.forward(rq["source"])
+            torch.cuda.synchronize()
+        assert r.fwd.iters == st.iters and torch.equal(r.E, E)
+    assert res["mixed"][0][1].fwd.iters != res["mixed"][0][0].fwd.iters or \
+        not torch.equal(res["mixed"][0][1].E, res["mixed"][0][0].E)
