@@ -120,6 +120,11 @@ int fh_order_z(int n, int ncol, int nth, int* order) {
   return (int)o.size();
 }
 
+// The z work model of an order (s radices).
+long long fh_z_balance(int n, const int* order, int s, int ncol, int nth) {
+  return z_balance_cost(std::vector<int>(order, order + s), n, ncol, nth);
+}
+
 // Wave numbers (p, q) per position (float2 [n]).
 int fh_pq(int n, int layout, int ncol, float* pq) {
   Axis A;

@@ -123,3 +123,9 @@ def test_z_radix_order_balances_the_warp_groups_rounds(fh):
     s = fh.fh_order_z(336, 8, 256, o)
     assert list(o[:s]) == [8, 6, 7]
     assert fh.fh_order_z(17, 8, 256, o) == -1
+    # the model by hand, 315 = 5 7 9 on 8-column tiles and 256 threads: stage 5 has 3 * 4 * 63
+    # = 756 pair items (3 rounds x 2 directions x 2 * 5 values = 60), stage 7 has 540 (3 x 2 x
+    # 14 = 84), the fused stage 9 has 8 * 35 = 280 single-column items (2 rounds x 6 * 9 = 108)
+    fh.fh_z_balance.restype = ctypes.c_longlong
+    assert fh.fh_z_balance(315, (ctypes.c_int * 3)(5, 7, 9), 3, 8, 256) == 252
+    assert fh.fh_z_balance(315, (ctypes.c_int * 3)(5, 9, 7), 3, 8, 256) == 60 + 2 * 2 * 18 + 2 * 42
